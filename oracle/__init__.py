@@ -1,0 +1,173 @@
+"""FP64 CPU oracle of the exact tetrahedron deposit -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product (``paper_1612_09491_gb300``)
+never imports it, and it never imports the product.
+
+``oracle.c`` is a plain C implementation of M[c] = sum_t m_t/|V_t| vol(T_t ∩ C_c)
+(Eq. 1 integrated over a cell) by the CPU deposit of Sec. 6.1 and the recursive
+tetrahedron split of Sec. 6.3.  ``exact.py`` holds an independent exact-rational
+evaluation (Lasserre's recursion) used only to pin the C oracle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_build/liboracle.so (gcc, -O2, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", "-Wall", "-Wextra",
+           "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True, stdout=sys.stderr, stderr=sys.stderr)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            i64p = ctypes.POINTER(ctypes.c_int64)
+            dp = ctypes.POINTER(ctypes.c_double)
+            fp = ctypes.POINTER(ctypes.c_float)
+            ip = ctypes.POINTER(ctypes.c_int)
+            L.oracle_deposit_lattice.argtypes = [fp, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                                 i64p, dp, i64p, ctypes.c_int64, ctypes.c_int, dp]
+            L.oracle_deposit_lattice.restype = ctypes.c_int
+            L.oracle_deposit_tets.argtypes = [dp, dp, ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                                              i64p, dp, dp]
+            L.oracle_deposit_tets.restype = ctypes.c_int
+            L.oracle_tet_box_volume.argtypes = [dp, dp, dp]
+            L.oracle_tet_box_volume.restype = ctypes.c_double
+            L.oracle_tet_halfspaces_volume.argtypes = [dp, ip, ip, dp, ctypes.c_int]
+            L.oracle_tet_halfspaces_volume.restype = ctypes.c_double
+            L.oracle_lattice_tet.argtypes = [fp, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_int64,
+                                             ctypes.c_int, dp]
+            L.oracle_lattice_tet.restype = ctypes.c_int
+            L.oracle_tet_cells.argtypes = [dp, dp, i64p, dp, ctypes.c_int64]
+            L.oracle_tet_cells.restype = ctypes.c_int64
+            L.oracle_tet_volume.argtypes = [dp]
+            L.oracle_tet_volume.restype = ctypes.c_double
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+STAT_KEYS = ("tets", "bbox_cells", "overlapped_cells", "partial_cells", "degenerate_tets",
+             "lost_mass", "threads")
+
+
+def deposit_lattice(pos: np.ndarray, n, grid_n, box: float = 1.0, periodic: bool = True,
+                    particle_mass: float | None = None, cube_ids=None, nthreads: int = 0):
+    """Cell masses [G2, G1, G0] (x fastest) of the lattice tessellation; returns (mass, stats)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(n, dtype=np.int64), (3,)))
+    g = np.ascontiguousarray(np.broadcast_to(np.asarray(grid_n, dtype=np.int64), (3,)))
+    if pos.shape != (int(np.prod(n)), 3):
+        raise ValueError("pos must be [n0*n1*n2, 3]")
+    if particle_mass is None:
+        particle_mass = 1.0 / float(np.prod(n))  # mean density 1 in a unit box
+    out = np.zeros(int(np.prod(g)), dtype=np.float64)
+    st = np.zeros(7, dtype=np.float64)
+    if cube_ids is not None:
+        cube_ids = np.ascontiguousarray(cube_ids, dtype=np.int64)
+        cptr, ncid = _ptr(cube_ids, ctypes.c_int64), cube_ids.size
+    else:
+        cptr, ncid = None, 0
+    rc = lib().oracle_deposit_lattice(_ptr(pos, ctypes.c_float), _ptr(n, ctypes.c_int64), box,
+                                      int(periodic), particle_mass, _ptr(g, ctypes.c_int64),
+                                      _ptr(out, ctypes.c_double), cptr, ncid, int(nthreads),
+                                      _ptr(st, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle_deposit_lattice failed: {rc}")
+    return out.reshape(int(g[2]), int(g[1]), int(g[0])), dict(zip(STAT_KEYS, st.tolist()))
+
+
+def deposit_tets(verts: np.ndarray, tet_mass, grid_n, box: float = 1.0, periodic: bool = True):
+    """Cell masses of explicit tetrahedra verts [T, 4, 3] (box units); returns (mass, stats)."""
+    verts = np.ascontiguousarray(verts, dtype=np.float64)
+    T = verts.shape[0]
+    tm = np.ascontiguousarray(np.broadcast_to(np.asarray(tet_mass, dtype=np.float64), (T,)))
+    g = np.ascontiguousarray(np.broadcast_to(np.asarray(grid_n, dtype=np.int64), (3,)))
+    out = np.zeros(int(np.prod(g)), dtype=np.float64)
+    st = np.zeros(7, dtype=np.float64)
+    rc = lib().oracle_deposit_tets(_ptr(verts, ctypes.c_double), _ptr(tm, ctypes.c_double), T, box,
+                                   int(periodic), _ptr(g, ctypes.c_int64), _ptr(out, ctypes.c_double),
+                                   _ptr(st, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle_deposit_tets failed: {rc}")
+    return out.reshape(int(g[2]), int(g[1]), int(g[0])), dict(zip(STAT_KEYS, st.tolist()))
+
+
+def tet_box_volume(tet, lo, hi) -> float:
+    t = np.ascontiguousarray(tet, dtype=np.float64).reshape(12)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    hi = np.ascontiguousarray(hi, dtype=np.float64)
+    return lib().oracle_tet_box_volume(_ptr(t, ctypes.c_double), _ptr(lo, ctypes.c_double),
+                                       _ptr(hi, ctypes.c_double))
+
+
+def tet_halfspaces_volume(tet, halfspaces) -> float:
+    """halfspaces: iterable of (axis, keep_below, s)."""
+    t = np.ascontiguousarray(tet, dtype=np.float64).reshape(12)
+    hs = list(halfspaces)
+    ax = np.array([h[0] for h in hs], dtype=np.intc)
+    kb = np.array([int(h[1]) for h in hs], dtype=np.intc)
+    s = np.array([h[2] for h in hs], dtype=np.float64)
+    return lib().oracle_tet_halfspaces_volume(_ptr(t, ctypes.c_double), _ptr(ax, ctypes.c_int),
+                                              _ptr(kb, ctypes.c_int), _ptr(s, ctypes.c_double), len(hs))
+
+
+def lattice_tet(pos, n, cube: int, s: int, box: float = 1.0, periodic: bool = True) -> np.ndarray:
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(n, dtype=np.int64), (3,)))
+    out = np.zeros(12, dtype=np.float64)
+    rc = lib().oracle_lattice_tet(_ptr(pos, ctypes.c_float), _ptr(n, ctypes.c_int64), box, int(periodic),
+                                  int(cube), int(s), _ptr(out, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError("oracle_lattice_tet failed")
+    return out.reshape(4, 3)
+
+
+def tet_cells(tet, h):
+    """All cells (ix, iy, iz) overlapped by one tetrahedron with their overlap volumes (no folding)."""
+    t = np.ascontiguousarray(tet, dtype=np.float64).reshape(12)
+    hh = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (3,)))
+    cap = 4096
+    while True:
+        cells = np.zeros((cap, 3), dtype=np.int64)
+        vols = np.zeros(cap, dtype=np.float64)
+        cnt = lib().oracle_tet_cells(_ptr(t, ctypes.c_double), _ptr(hh, ctypes.c_double),
+                                     _ptr(cells, ctypes.c_int64), _ptr(vols, ctypes.c_double), cap)
+        if cnt < 0:
+            raise RuntimeError("oracle_tet_cells failed")
+        if cnt <= cap:
+            return cells[:cnt].copy(), vols[:cnt].copy()
+        cap = int(cnt)
+
+
+def tet_volume(tet) -> float:
+    t = np.ascontiguousarray(tet, dtype=np.float64).reshape(12)
+    return lib().oracle_tet_volume(_ptr(t, ctypes.c_double))
