@@ -1,0 +1,187 @@
+/*
+ * pse.h -- C ABI of the GB300 (sm_103a) exact tetrahedron-deposit library.
+ *
+ * The phase-space-element density of Kaehler (arXiv:1612.09491), Sec. 2, Eq. 1:
+ * tracer particles sit on a Lagrangian lattice; each Lagrangian cube of 8
+ * neighbouring particles is split into 6 tetrahedra of mass m_p/6, and the
+ * density at x is m * sum_i 1/V_i(x) over the tetrahedra covering x.  Integrated
+ * over a deposit cell C that is
+ *
+ *     M[C] = sum_t (m_t / |V_t|) * vol(T_t  intersect  C),
+ *
+ * which every deposit entry point below computes exactly (up to rounding):
+ * each tetrahedron is clipped against every cell it overlaps (Sec. 6.3).
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ *  - Pointers prefixed d_ are DEVICE memory owned by the caller; h_ are HOST
+ *    memory owned by the caller.  The library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued asynchronously on it.  An entry point that
+ *    returns host-side results (h_stats, h_n_tets, octree metadata)
+ *    synchronises `stream` before returning; the others do not.
+ *  - Positions: float32 [n0*n1*n2][3], particle (i,j,k) at flat index
+ *    i + n0*(j + n1*k) (x fastest: the particle IDs' Lagrangian order, Sec. 3).
+ *  - Tessellation: the Kuhn split of each Lagrangian cube around its 000-111
+ *    diagonal (the paper uses "6 tetrahedra" without fixing which, Sec. 2):
+ *    tetrahedron s (0..5) of cube (i,j,k) visits corners 000, e_a, e_a+e_b, 111
+ *    for the axis permutation (a,b,c) = xyz, xzy, yxz, yzx, zxy, zyx.
+ *    Its id is 6*cube + s, with cube = i + n0*(j + n1*k) (periodic lattices)
+ *    or i + (n0-1)*(j + (n1-1)*k) (open lattices).
+ *  - Periodic boxes: every cube corner is unwrapped to the periodic image
+ *    nearest to corner 000; deposit cells are folded modulo the grid size.
+ *  - Grids: cubic box [0, box)^3 split into g0*g1*g2 cells; cell (ix,iy,iz) covers
+ *    [ix*h0,(ix+1)*h0) x ... with h_a = box/g_a; cell masses are float64 at flat
+ *    index ix + g0*(iy + g1*iz).  Density = mass / (h0*h1*h2).
+ *  - A tetrahedron whose float64 volume is exactly zero deposits all of its
+ *    mass into the cell that contains its vertex centroid.
+ *  - Return value: PSE_OK (0) or a negative PSE_ERR_* code; the message of the
+ *    last failure on the calling host thread is pse_last_error().
+ *  - Calls are safe to run concurrently when they use distinct streams, output
+ *    buffers and workspaces.
+ */
+#ifndef PSE_H_
+#define PSE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PSE_API __attribute__((visibility("default")))
+#else
+#define PSE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSE_ABI_VERSION 1
+
+#define PSE_OK 0
+#define PSE_ERR_INVALID_ARG -1 /* a null pointer, a bad size or an inconsistent option */
+#define PSE_ERR_CUDA -2        /* a CUDA runtime call failed (message in pse_last_error) */
+#define PSE_ERR_OOM -3         /* the library could not allocate device or host memory */
+#define PSE_ERR_TIMEOUT -4     /* a bounded device-side wait ran out (spin_limit) */
+#define PSE_ERR_UNSUPPORTED -5 /* a valid request this build does not implement */
+#define PSE_ERR_WORKSPACE -6   /* ws_bytes smaller than pse_workspace_size() */
+#define PSE_ERR_DEVICE -7      /* a device-side check failed (e.g. a tetrahedron wider than box/2) */
+
+/* precision (pse_deposit_opts.precision) */
+#define PSE_FP64_PLAIN 0   /* every step in float64 */
+#define PSE_FP32_FP64ACC 1 /* float32 clip with float64 redo of guarded clips; float64 accumulation */
+
+/* schedule (pse_deposit_opts.schedule) */
+#define PSE_THREAD_PER_TET 0    /* one thread per tetrahedron (the plain baseline) */
+#define PSE_WARP_COOPERATIVE 1  /* one warp per batch of tetrahedra, lanes over (tet, cell) pairs */
+#define PSE_BINNED_PERSISTENT 2 /* size-binned persistent kernel (bins from bbox count or cost model) */
+
+/* operation ids for pse_workspace_size */
+#define PSE_OP_DEPOSIT_UNIFORM 1
+#define PSE_OP_DEPOSIT_OCTREE 2
+#define PSE_OP_BUILD_OCTREE 3
+#define PSE_OP_DEPOSIT_TETS 4
+
+typedef struct pse_lattice {
+    int64_t n[3];         /* particles per axis (>= 2 each) */
+    double box;           /* side of the cubic box, > 0 */
+    int32_t periodic;     /* 1: periodic lattice and grid; 0: open (cells outside the grid are dropped) */
+    int32_t reserved;
+    double particle_mass; /* m_p; every tetrahedron carries m_p/6 */
+} pse_lattice;
+
+typedef struct pse_deposit_opts {
+    int32_t precision;       /* PSE_FP64_PLAIN or PSE_FP32_FP64ACC */
+    int32_t schedule;        /* PSE_THREAD_PER_TET, PSE_WARP_COOPERATIVE or PSE_BINNED_PERSISTENT */
+    const void *cost_model;  /* nullable device pointer to trained cost-model weights (binned schedule) */
+    const void *tuning;      /* nullable host pointer to a pse_tuning block; NULL = built-in defaults */
+    double guard_eps;        /* FP32 clip guard: redo a tetrahedron's clips in float64 when the
+                                estimated relative error of its FP32 clip exceeds guard_eps (<=0: default) */
+    int64_t spin_limit;      /* iteration bound of every device-side wait (<=0: default) */
+    int32_t accumulate;      /* 0: the call overwrites the output; 1: it adds to it */
+    int32_t mass_fixup;      /* FP32 path: 1 adds each tetrahedron's rounding residual m_t - sum(deposits)
+                                to the cell of its centroid, so total mass is conserved to float64 rounding */
+    const int64_t *d_cube_ids; /* nullable: deposit only these Lagrangian cubes (device int64 [n_cube_ids]) */
+    int64_t n_cube_ids;
+} pse_deposit_opts;
+
+typedef struct pse_deposit_stats {
+    uint64_t tets;             /* tetrahedra processed */
+    uint64_t bbox_cells;       /* (tetrahedron, cell) pairs inside bounding boxes */
+    uint64_t inside_cells;     /* pairs classified "cell inside tetrahedron" */
+    uint64_t partial_clips;    /* pairs that went through the exact clip */
+    uint64_t fp64_redos;       /* clips re-done in float64 by the guard */
+    uint64_t degenerate_tets;  /* zero-volume tetrahedra (centroid rule) */
+    uint64_t single_cell_tets; /* tetrahedra whose bounding box is one cell */
+    uint64_t bin_counts[8];    /* binned schedule: tetrahedra per size bin */
+    double mass_in;            /* sum of m_t over the processed tetrahedra */
+    double mass_dropped;       /* open grids: mass that fell outside the grid */
+} pse_deposit_stats;
+
+typedef struct pse_tuning {
+    int32_t blocks_per_sm;   /* resident blocks per SM of the persistent kernels */
+    int32_t warps_per_block;
+    int32_t bin_edges[7];    /* bbox-cell-count upper edges of bins 0..6 (bin 7 is the rest) */
+    int32_t reserved;
+} pse_tuning;
+
+/*
+ * Build the tetrahedra of the Lagrangian tessellation (Sec. 2: 6 tetrahedra per
+ * Lagrangian cube) from a lattice of particle positions.
+ *   d_pos       float32 [n0*n1*n2][3] device, read only.
+ *   d_tet_vidx  nullable int32 [T][4] device: particle indices of vertices v0..v3.
+ *   d_tet_vol   nullable float32 [T] device: signed volume (box units^3, periodic unwrap applied).
+ *   h_n_tets    nullable host: receives T = 6 * number of cubes.
+ * Synchronises `stream` only if h_n_tets is non-null.  T must fit int32 when d_tet_vidx is
+ * requested (PSE_ERR_INVALID_ARG otherwise).
+ */
+PSE_API int pse_build_tets_from_lagrangian_grid(const float *d_pos, const pse_lattice *lat, int32_t *d_tet_vidx,
+                                        float *d_tet_vol, int64_t *h_n_tets, void *stream);
+
+/*
+ * Deposit the whole tessellation (or the cubes in opts->d_cube_ids) onto a uniform
+ * grid: d_cell_mass[ix + g0*(iy + g1*iz)] (+)= sum_t m_t/|V_t| vol(T_t ∩ C)  (Eq. 1
+ * over cells; the clip is Sec. 6.3's operation, computed here by half-space clipping
+ * and the divergence theorem).
+ *   grid_n      host int64[3], cells per axis (>= 1 each).
+ *   d_cell_mass float64 [g0*g1*g2] device, written (accumulate = 0) or added to.
+ *   opts        nullable: NULL = PSE_FP32_FP64ACC, PSE_WARP_COOPERATIVE, overwrite, mass fix-up on.
+ *   h_stats     nullable host: filled with counters; when non-null the call synchronises.
+ *   d_ws        device workspace of ws_bytes >= pse_workspace_size(PSE_OP_DEPOSIT_UNIFORM, lat, grid_n);
+ *               NULL with ws_bytes = 0 makes the library allocate it stream-ordered for this call.
+ */
+PSE_API int pse_deposit_uniform(const float *d_pos, const pse_lattice *lat, const int64_t grid_n[3],
+                        double *d_cell_mass, const pse_deposit_opts *opts, pse_deposit_stats *h_stats,
+                        void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Deposit explicit tetrahedra (test and tooling entry point; the same kernels as
+ * pse_deposit_uniform with a different tetrahedron source).
+ *   d_verts    float32 [n_tets][4][3] device, box units, already unwrapped.
+ *   d_tet_mass float64 [n_tets] device: m_t of each tetrahedron.
+ *   box, periodic, grid_n, d_cell_mass, opts, h_stats, d_ws, ws_bytes, stream: as above
+ *   (opts->d_cube_ids must be NULL).
+ */
+PSE_API int pse_deposit_tets(const float *d_verts, const double *d_tet_mass, int64_t n_tets, double box,
+                     int32_t periodic, const int64_t grid_n[3], double *d_cell_mass,
+                     const pse_deposit_opts *opts, pse_deposit_stats *h_stats, void *d_ws,
+                     size_t ws_bytes, void *stream);
+
+/*
+ * Bytes of device workspace an operation needs.  op = PSE_OP_*; lat may be NULL for
+ * PSE_OP_DEPOSIT_TETS; op_params: for the uniform/tets deposits a host int64[3] grid_n
+ * (may be NULL).  Returns 0 for an unknown op.
+ */
+PSE_API size_t pse_workspace_size(int op, const pse_lattice *lat, const void *op_params);
+
+/* Message of the last failed call on this host thread ("" if none).  Never NULL. */
+PSE_API const char *pse_last_error(void);
+
+/* PSE_ABI_VERSION of the loaded library. */
+PSE_API int pse_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSE_H_ */

@@ -1,0 +1,152 @@
+"""GB300 (sm_103a) exact tetrahedron deposit of the phase-space-element method.
+
+Thin torch-facing wrappers of the C ABI (include/pse.h); names follow the ABI
+without its ``pse_`` prefix.  Tensors must live on the current CUDA device; the
+work is enqueued on the current torch stream (or ``stream=``).  Nothing here
+computes: every step runs in libpse.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    PSE_BINNED_PERSISTENT,
+    PSE_FP32_FP64ACC,
+    PSE_FP64_PLAIN,
+    PSE_THREAD_PER_TET,
+    PSE_WARP_COOPERATIVE,
+    PseError,
+)
+
+__all__ = ["build_tets_from_lagrangian_grid", "deposit_uniform", "deposit_tets", "workspace_size", "last_error",
+           "abi_version", "lattice", "opts"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def lattice(n, box: float = 1.0, periodic: bool = True, particle_mass: float | None = None) -> _lib.Lattice:
+    n3 = (n, n, n) if isinstance(n, int) else tuple(int(x) for x in n)
+    if particle_mass is None:
+        particle_mass = box ** 3 / float(n3[0] * n3[1] * n3[2])  # mean density 1
+    lat = _lib.Lattice()
+    lat.n[:] = n3
+    lat.box = float(box)
+    lat.periodic = 1 if periodic else 0
+    lat.particle_mass = float(particle_mass)
+    return lat
+
+
+def opts(precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
+         accumulate: bool = False, mass_fixup: bool = True, cube_ids=None) -> _lib.DepositOpts:
+    o = _lib.DepositOpts()
+    o.precision = precision
+    o.schedule = schedule
+    o.guard_eps = guard_eps
+    o.accumulate = 1 if accumulate else 0
+    o.mass_fixup = 1 if mass_fixup else 0
+    if cube_ids is not None:
+        o.d_cube_ids = _dev_ptr(cube_ids, _torch().int64, "cube_ids").value
+        o.n_cube_ids = cube_ids.numel()
+    return o
+
+
+def _grid3(grid_n):
+    g = (grid_n,) * 3 if isinstance(grid_n, int) else tuple(int(x) for x in grid_n)
+    return (ctypes.c_int64 * 3)(*g), g
+
+
+def deposit_uniform(pos, n, grid_n, *, box: float = 1.0, periodic: bool = True, particle_mass=None, out=None,
+                    precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
+                    accumulate: bool = False, mass_fixup: bool = True, cube_ids=None, stats: bool = False,
+                    workspace=None, stream=None):
+    """pse_deposit_uniform: cell masses float64 [g2, g1, g0] (x fastest)."""
+    torch = _torch()
+    L = _lib.load()
+    lat = lattice(n, box, periodic, particle_mass)
+    g3, g = _grid3(grid_n)
+    if out is None:
+        out = torch.empty((g[2], g[1], g[0]), dtype=torch.float64, device=pos.device)
+    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, cube_ids)
+    st = _lib.DepositStats() if stats else None
+    ws_ptr, ws_bytes = (ctypes.c_void_p(None), 0) if workspace is None else \
+        (_dev_ptr(workspace, torch.uint8, "workspace"), workspace.numel())
+    rc = L.pse_deposit_uniform(_dev_ptr(pos, torch.float32, "pos"), ctypes.byref(lat), g3,
+                               _dev_ptr(out, torch.float64, "out"), ctypes.byref(o),
+                               ctypes.byref(st) if st is not None else None, ws_ptr, ws_bytes, _stream_ptr(stream))
+    _lib.check(rc)
+    return (out, st.to_dict()) if stats else out
+
+
+def deposit_tets(verts, tet_mass, grid_n, *, box: float = 1.0, periodic: bool = True, out=None,
+                 precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
+                 accumulate: bool = False, mass_fixup: bool = True, stats: bool = False, workspace=None, stream=None):
+    """pse_deposit_tets: explicit tetrahedra verts float32 [T, 4, 3] (box units), masses float64 [T]."""
+    torch = _torch()
+    L = _lib.load()
+    g3, g = _grid3(grid_n)
+    if out is None:
+        out = torch.empty((g[2], g[1], g[0]), dtype=torch.float64, device=verts.device)
+    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup)
+    st = _lib.DepositStats() if stats else None
+    ws_ptr, ws_bytes = (ctypes.c_void_p(None), 0) if workspace is None else \
+        (_dev_ptr(workspace, torch.uint8, "workspace"), workspace.numel())
+    T = verts.shape[0]
+    rc = L.pse_deposit_tets(_dev_ptr(verts, torch.float32, "verts"), _dev_ptr(tet_mass, torch.float64, "tet_mass"),
+                            T, float(box), 1 if periodic else 0, g3, _dev_ptr(out, torch.float64, "out"),
+                            ctypes.byref(o), ctypes.byref(st) if st is not None else None, ws_ptr, ws_bytes,
+                            _stream_ptr(stream))
+    _lib.check(rc)
+    return (out, st.to_dict()) if stats else out
+
+
+def build_tets_from_lagrangian_grid(pos, n, *, box: float = 1.0, periodic: bool = True, want_vidx: bool = True,
+                                    want_vol: bool = True, stream=None):
+    """pse_build_tets_from_lagrangian_grid: (vidx int32 [T,4] or None, signed vol float32 [T] or None)."""
+    torch = _torch()
+    L = _lib.load()
+    lat = lattice(n, box, periodic)
+    nt = ctypes.c_int64(0)
+    _lib.check(L.pse_build_tets_from_lagrangian_grid(_dev_ptr(pos, torch.float32, "pos"), ctypes.byref(lat), None,
+                                                     None, ctypes.byref(nt), _stream_ptr(stream)))
+    T = nt.value
+    vidx = torch.empty((T, 4), dtype=torch.int32, device=pos.device) if want_vidx else None
+    vol = torch.empty((T,), dtype=torch.float32, device=pos.device) if want_vol else None
+    _lib.check(L.pse_build_tets_from_lagrangian_grid(
+        _dev_ptr(pos, torch.float32, "pos"), ctypes.byref(lat),
+        _dev_ptr(vidx, torch.int32, "vidx") if vidx is not None else None,
+        _dev_ptr(vol, torch.float32, "vol") if vol is not None else None, None, _stream_ptr(stream)))
+    return vidx, vol
+
+
+def workspace_size(op: int = _lib.PSE_OP_DEPOSIT_UNIFORM, lat=None) -> int:
+    return int(_lib.load().pse_workspace_size(op, ctypes.byref(lat) if lat is not None else None, None))
+
+
+def last_error() -> str:
+    return _lib.load().pse_last_error().decode()
+
+
+def abi_version() -> int:
+    return int(_lib.load().pse_abi_version())

@@ -1,0 +1,119 @@
+"""ctypes binding of the C ABI in include/pse.h (argument marshalling only).
+
+Every step of the deposit runs in libpse.so's CUDA kernels; this module only
+turns torch tensors into device pointers and the current CUDA stream into the
+``stream`` argument.  If the library has not been built, importing the functions
+raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PSE_OK = 0
+PSE_ERR_INVALID_ARG = -1
+PSE_ERR_CUDA = -2
+PSE_ERR_OOM = -3
+PSE_ERR_TIMEOUT = -4
+PSE_ERR_UNSUPPORTED = -5
+PSE_ERR_WORKSPACE = -6
+PSE_ERR_DEVICE = -7
+
+PSE_FP64_PLAIN = 0
+PSE_FP32_FP64ACC = 1
+PSE_THREAD_PER_TET = 0
+PSE_WARP_COOPERATIVE = 1
+PSE_BINNED_PERSISTENT = 2
+
+PSE_OP_DEPOSIT_UNIFORM = 1
+PSE_OP_DEPOSIT_OCTREE = 2
+PSE_OP_BUILD_OCTREE = 3
+PSE_OP_DEPOSIT_TETS = 4
+
+# every symbol include/pse.h declares (checked by the tests)
+EXPORTED = (
+    "pse_build_tets_from_lagrangian_grid",
+    "pse_deposit_uniform",
+    "pse_deposit_tets",
+    "pse_workspace_size",
+    "pse_last_error",
+    "pse_abi_version",
+)
+
+
+class Lattice(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64 * 3), ("box", ctypes.c_double), ("periodic", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("particle_mass", ctypes.c_double)]
+
+
+class DepositOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("schedule", ctypes.c_int32), ("cost_model", ctypes.c_void_p),
+                ("tuning", ctypes.c_void_p), ("guard_eps", ctypes.c_double), ("spin_limit", ctypes.c_int64),
+                ("accumulate", ctypes.c_int32), ("mass_fixup", ctypes.c_int32), ("d_cube_ids", ctypes.c_void_p),
+                ("n_cube_ids", ctypes.c_int64)]
+
+
+class DepositStats(ctypes.Structure):
+    _fields_ = [("tets", ctypes.c_uint64), ("bbox_cells", ctypes.c_uint64), ("inside_cells", ctypes.c_uint64),
+                ("partial_clips", ctypes.c_uint64), ("fp64_redos", ctypes.c_uint64),
+                ("degenerate_tets", ctypes.c_uint64), ("single_cell_tets", ctypes.c_uint64),
+                ("bin_counts", ctypes.c_uint64 * 8), ("mass_in", ctypes.c_double), ("mass_dropped", ctypes.c_double)]
+
+    def to_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "bin_counts"}
+        d["bin_counts"] = list(self.bin_counts)
+        return d
+
+
+class PseError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pse error {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """The loaded libpse.so.  Raises if it is missing (build it with build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing: the CUDA library has not been built "
+                                   "(run paper_1612_09491_gb300.build.build())")
+            _build.build()
+        L = ctypes.CDLL(path)
+        vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+        L.pse_build_tets_from_lagrangian_grid.argtypes = [vp, ctypes.POINTER(Lattice), vp, vp, i64p, vp]
+        L.pse_deposit_uniform.argtypes = [vp, ctypes.POINTER(Lattice), i64p, vp, ctypes.POINTER(DepositOpts),
+                                          ctypes.POINTER(DepositStats), vp, ctypes.c_size_t, vp]
+        L.pse_deposit_tets.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, i64p, vp,
+                                       ctypes.POINTER(DepositOpts), ctypes.POINTER(DepositStats), vp, ctypes.c_size_t,
+                                       vp]
+        L.pse_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Lattice), vp]
+        L.pse_workspace_size.restype = ctypes.c_size_t
+        L.pse_last_error.argtypes = []
+        L.pse_last_error.restype = ctypes.c_char_p
+        L.pse_abi_version.argtypes = []
+        for name in ("pse_build_tets_from_lagrangian_grid", "pse_deposit_uniform", "pse_deposit_tets",
+                     "pse_abi_version"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return _lib
+
+
+def check(rc: int):
+    if rc != PSE_OK:
+        raise PseError(rc, load().pse_last_error().decode())

@@ -1,0 +1,292 @@
+// abi.cu -- extern "C" entry points declared in include/pse.h: argument checks,
+// workspace handling, launches and the host-side readback of counters.
+#include <cfloat>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/pse.h"
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(PSE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+pse_deposit_opts default_opts()
+{
+    pse_deposit_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.precision = PSE_FP32_FP64ACC;
+    o.schedule = PSE_WARP_COOPERATIVE;
+    o.guard_eps = 0.0;
+    o.spin_limit = 0;
+    o.accumulate = 0;
+    o.mass_fixup = 1;
+    return o;
+}
+
+// FP32 guard: a tetrahedron whose conditioning estimate kappa (surface * longest edge /
+// |6V|) times the float32 unit roundoff exceeds guard_eps is clipped in float64.
+constexpr double kDefaultGuardEps = 2.0e-5;
+
+float kappa_limit(double guard_eps)
+{
+    const double g = guard_eps > 0.0 ? guard_eps : kDefaultGuardEps;
+    return (float)(g / (double)FLT_EPSILON);
+}
+
+struct WsLease {
+    pse::Workspace *ws = nullptr;
+    bool owned = false;
+    cudaStream_t st = nullptr;
+    ~WsLease()
+    {
+        if (owned && ws) cudaFreeAsync(ws, st);
+    }
+};
+
+int acquire_ws(void *d_ws, size_t ws_bytes, cudaStream_t st, WsLease &lease)
+{
+    lease.st = st;
+    if (d_ws == nullptr) {
+        if (ws_bytes != 0) return fail(PSE_ERR_INVALID_ARG, "d_ws is NULL but ws_bytes is %zu", ws_bytes);
+        void *p = nullptr;
+        cudaError_t e = cudaMallocAsync(&p, pse::kWorkspaceBytes, st);
+        if (e != cudaSuccess) return fail(PSE_ERR_OOM, "workspace allocation failed: %s", cudaGetErrorString(e));
+        lease.ws = static_cast<pse::Workspace *>(p);
+        lease.owned = true;
+    } else {
+        if (ws_bytes < pse::kWorkspaceBytes)
+            return fail(PSE_ERR_WORKSPACE, "ws_bytes = %zu < required %zu", ws_bytes, pse::kWorkspaceBytes);
+        if (reinterpret_cast<uintptr_t>(d_ws) % 16 != 0) return fail(PSE_ERR_INVALID_ARG, "d_ws must be 16-byte aligned");
+        lease.ws = static_cast<pse::Workspace *>(d_ws);
+    }
+    cudaError_t e = cudaMemsetAsync(lease.ws, 0, pse::kWorkspaceBytes, st);
+    if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+    return PSE_OK;
+}
+
+int check_grid(const int64_t grid_n[3], int64_t &cells)
+{
+    if (!grid_n) return fail(PSE_ERR_INVALID_ARG, "grid_n is NULL");
+    cells = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (grid_n[a] < 1 || grid_n[a] > (int64_t(1) << 24))
+            return fail(PSE_ERR_INVALID_ARG, "grid_n[%d] = %lld out of range [1, 2^24]", a, (long long)grid_n[a]);
+        cells *= grid_n[a];
+    }
+    return PSE_OK;
+}
+
+int check_opts(const pse_deposit_opts &o)
+{
+    if (o.precision != PSE_FP64_PLAIN && o.precision != PSE_FP32_FP64ACC)
+        return fail(PSE_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+    if (o.schedule != PSE_THREAD_PER_TET && o.schedule != PSE_WARP_COOPERATIVE && o.schedule != PSE_BINNED_PERSISTENT)
+        return fail(PSE_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
+    if (o.schedule == PSE_BINNED_PERSISTENT) return fail(PSE_ERR_UNSUPPORTED, "PSE_BINNED_PERSISTENT is not available");
+    if (o.schedule == PSE_WARP_COOPERATIVE && o.precision != PSE_FP32_FP64ACC)
+        return fail(PSE_ERR_UNSUPPORTED, "the warp-cooperative schedule runs the FP32 clip (precision 1)");
+    if (o.n_cube_ids < 0) return fail(PSE_ERR_INVALID_ARG, "n_cube_ids < 0");
+    if (o.n_cube_ids > 0 && !o.d_cube_ids) return fail(PSE_ERR_INVALID_ARG, "n_cube_ids > 0 but d_cube_ids is NULL");
+    return PSE_OK;
+}
+
+void fill_grid(pse::DepositParams &p, const int64_t grid_n[3], double box)
+{
+    for (int a = 0; a < 3; ++a) {
+        p.g[a] = grid_n[a];
+        p.scale_d[a] = (double)grid_n[a] / box;
+        p.scale_f[a] = (float)p.scale_d[a];
+    }
+}
+
+int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells, pse_deposit_stats *h_stats,
+                void *d_ws, size_t ws_bytes, cudaStream_t st)
+{
+    WsLease lease;
+    int rc = acquire_ws(d_ws, ws_bytes, st, lease);
+    if (rc != PSE_OK) return rc;
+    p.ws = lease.ws;
+    p.kappa_max = kappa_limit(o.guard_eps);
+    p.fixup = o.mass_fixup ? 1 : 0;
+    cudaError_t e;
+    if (!o.accumulate) {
+        e = cudaMemsetAsync(p.out, 0, (size_t)cells * sizeof(double), st);
+        if (e != cudaSuccess) return cuda_fail(e, "output clear");
+    }
+    const bool stats = h_stats != nullptr;
+    if (p.n_units > 0) {
+        if (o.schedule == PSE_THREAD_PER_TET) {
+            e = pse::launch_thread_per_tet(p, o.precision == PSE_FP64_PLAIN, stats, st);
+        } else {
+            p.n_items = (p.src == pse::SRC_LATTICE) ? ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2] : (p.n_units + 31) / 32;
+            e = pse::launch_warp_coop(p, stats, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+    }
+    if (stats) {
+        pse::Workspace hw;
+        e = cudaMemcpyAsync(&hw, lease.ws, sizeof(hw), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "stats readback");
+        std::memset(h_stats, 0, sizeof(*h_stats));
+        h_stats->tets = hw.stats[pse::ST_TETS];
+        h_stats->bbox_cells = hw.stats[pse::ST_BBOX_CELLS];
+        h_stats->inside_cells = hw.stats[pse::ST_INSIDE_CELLS];
+        h_stats->partial_clips = hw.stats[pse::ST_PARTIAL_CLIPS];
+        h_stats->fp64_redos = hw.stats[pse::ST_FP64_REDOS];
+        h_stats->degenerate_tets = hw.stats[pse::ST_DEGENERATE];
+        h_stats->single_cell_tets = hw.stats[pse::ST_SINGLE_CELL];
+        for (int b = 0; b < 8; ++b) h_stats->bin_counts[b] = hw.stats[pse::ST_BIN0 + b];
+        h_stats->mass_in = hw.mass_in;
+        h_stats->mass_dropped = hw.mass_dropped;
+        if (hw.error_code != 0)
+            return fail(PSE_ERR_DEVICE,
+                        hw.error_code == 1 ? "a tetrahedron is wider than the periodic grid (detail %d)"
+                        : hw.error_code == 2 ? "a tetrahedron overlaps more than 2^25 cells (detail %d)"
+                        : hw.error_code == 3 ? "a cube id is out of range (work unit %d)"
+                        : hw.error_code == 4 ? "non-finite or out-of-range vertex coordinates (detail %d)"
+                                             : "device-side check failed (detail %d)",
+                        hw.error_detail);
+    }
+    return PSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pse_last_error(void) { return g_last_error.c_str(); }
+
+int pse_abi_version(void) { return PSE_ABI_VERSION; }
+
+size_t pse_workspace_size(int op, const pse_lattice *lat, const void *op_params)
+{
+    (void)lat;
+    (void)op_params;
+    switch (op) {
+    case PSE_OP_DEPOSIT_UNIFORM:
+    case PSE_OP_DEPOSIT_TETS:
+        return pse::kWorkspaceBytes;
+    default:
+        return 0;
+    }
+}
+
+int pse_build_tets_from_lagrangian_grid(const float *d_pos, const pse_lattice *lat, int32_t *d_tet_vidx,
+                                        float *d_tet_vol, int64_t *h_n_tets, void *stream)
+{
+    g_last_error.clear();
+    if (!d_pos || !lat) return fail(PSE_ERR_INVALID_ARG, "d_pos and lat must be non-NULL");
+    for (int a = 0; a < 3; ++a)
+        if (lat->n[a] < 2) return fail(PSE_ERR_INVALID_ARG, "lat->n[%d] = %lld < 2", a, (long long)lat->n[a]);
+    if (!(lat->box > 0.0) || !std::isfinite(lat->box)) return fail(PSE_ERR_INVALID_ARG, "lat->box must be > 0");
+    int64_t nc[3];
+    for (int a = 0; a < 3; ++a) nc[a] = lat->periodic ? lat->n[a] : lat->n[a] - 1;
+    const int64_t n_tets = 6 * nc[0] * nc[1] * nc[2];
+    if (d_tet_vidx && lat->n[0] * lat->n[1] * lat->n[2] > INT32_MAX)
+        return fail(PSE_ERR_INVALID_ARG, "particle indices do not fit int32");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (d_tet_vidx || d_tet_vol) {
+        cudaError_t e = pse::launch_build_tets(d_pos, lat->n, nc, lat->periodic, lat->box, d_tet_vidx, d_tet_vol, n_tets, st);
+        if (e != cudaSuccess) return cuda_fail(e, "build_tets launch");
+    }
+    if (h_n_tets) {
+        *h_n_tets = n_tets;
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "build_tets");
+    }
+    return PSE_OK;
+}
+
+int pse_deposit_uniform(const float *d_pos, const pse_lattice *lat, const int64_t grid_n[3], double *d_cell_mass,
+                        const pse_deposit_opts *opts, pse_deposit_stats *h_stats, void *d_ws, size_t ws_bytes,
+                        void *stream)
+{
+    g_last_error.clear();
+    if (!d_pos || !lat || !d_cell_mass) return fail(PSE_ERR_INVALID_ARG, "d_pos, lat and d_cell_mass must be non-NULL");
+    for (int a = 0; a < 3; ++a)
+        if (lat->n[a] < 2) return fail(PSE_ERR_INVALID_ARG, "lat->n[%d] = %lld < 2", a, (long long)lat->n[a]);
+    if (!(lat->box > 0.0) || !std::isfinite(lat->box)) return fail(PSE_ERR_INVALID_ARG, "lat->box must be > 0");
+    if (!std::isfinite(lat->particle_mass)) return fail(PSE_ERR_INVALID_ARG, "lat->particle_mass must be finite");
+    int64_t cells = 0;
+    int rc = check_grid(grid_n, cells);
+    if (rc != PSE_OK) return rc;
+    const pse_deposit_opts o = opts ? *opts : default_opts();
+    rc = check_opts(o);
+    if (rc != PSE_OK) return rc;
+
+    pse::DepositParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.periodic = lat->periodic ? 1 : 0;
+    p.pos = d_pos;
+    for (int a = 0; a < 3; ++a) {
+        p.n[a] = lat->n[a];
+        p.nc[a] = p.periodic ? lat->n[a] : lat->n[a] - 1;
+    }
+    p.box = lat->box;
+    p.m_tet = lat->particle_mass / 6.0;
+    fill_grid(p, grid_n, lat->box);
+    p.out = d_cell_mass;
+    if (o.d_cube_ids) {
+        p.src = pse::SRC_CUBE_LIST;
+        p.cube_ids = o.d_cube_ids;
+        p.n_units = o.n_cube_ids;
+    } else {
+        p.src = pse::SRC_LATTICE;
+        p.n_units = p.nc[0] * p.nc[1] * p.nc[2];
+    }
+    return run_deposit(p, o, cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int pse_deposit_tets(const float *d_verts, const double *d_tet_mass, int64_t n_tets, double box, int32_t periodic,
+                     const int64_t grid_n[3], double *d_cell_mass, const pse_deposit_opts *opts,
+                     pse_deposit_stats *h_stats, void *d_ws, size_t ws_bytes, void *stream)
+{
+    g_last_error.clear();
+    if (n_tets < 0) return fail(PSE_ERR_INVALID_ARG, "n_tets < 0");
+    if ((n_tets > 0 && (!d_verts || !d_tet_mass)) || !d_cell_mass)
+        return fail(PSE_ERR_INVALID_ARG, "d_verts, d_tet_mass and d_cell_mass must be non-NULL");
+    if (!(box > 0.0) || !std::isfinite(box)) return fail(PSE_ERR_INVALID_ARG, "box must be > 0");
+    int64_t cells = 0;
+    int rc = check_grid(grid_n, cells);
+    if (rc != PSE_OK) return rc;
+    const pse_deposit_opts o = opts ? *opts : default_opts();
+    rc = check_opts(o);
+    if (rc != PSE_OK) return rc;
+    if (o.d_cube_ids) return fail(PSE_ERR_INVALID_ARG, "d_cube_ids applies to lattices only");
+
+    pse::DepositParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.src = pse::SRC_TETS;
+    p.periodic = periodic ? 1 : 0;
+    p.verts = d_verts;
+    p.tet_mass = d_tet_mass;
+    p.n_units = n_tets;
+    p.box = box;
+    fill_grid(p, grid_n, box);
+    p.out = d_cell_mass;
+    return run_deposit(p, o, cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

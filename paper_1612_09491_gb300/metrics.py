@@ -1,0 +1,23 @@
+"""Cell-mass error measures used to state the accuracy of every result.
+
+max_rel: max_c |M[c] - R[c]| / max(R[c], floor * mean(R))   (floor = 1e-3)
+l1:      sum_c |M[c] - R[c]| / sum_c R[c]
+mass:    |sum M - sum R| / sum R
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def cell_errors(m, ref, floor: float = 1e-3) -> dict:
+    m = np.asarray(m, dtype=np.float64).ravel()
+    r = np.asarray(ref, dtype=np.float64).ravel()
+    d = np.abs(m - r)
+    tot = r.sum()
+    mean = tot / max(r.size, 1)
+    den = np.maximum(r, floor * mean) if mean > 0 else np.ones_like(r)
+    return {
+        "max_rel": float((d / den).max()) if d.size else 0.0,
+        "l1": float(d.sum() / tot) if tot > 0 else float(d.sum()),
+        "mass": float(abs(m.sum() - tot) / tot) if tot > 0 else float(abs(m.sum())),
+    }

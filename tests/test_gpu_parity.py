@@ -1,0 +1,324 @@
+"""Parity of the CUDA deposit (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (the C13 measures of paper_1612_09491_gb300.metrics):
+  * FP64 plain path:     max_rel <= 1e-10 (different clip algorithm, both float64);
+  * FP32 + FP64-redo:    max_rel <= 1e-5 per cell, total mass <= 1e-12 relative.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_1612_09491_gb300 as pse  # noqa: E402
+from paper_1612_09491_gb300.metrics import cell_errors  # noqa: E402
+from pse_inputs import (CONFIGS, config_positions, jitter_positions, lattice_positions,  # noqa: E402
+                        random_dyadic_tets, zeldovich_positions)
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+MASS32 = 1e-12
+
+PATHS = [
+    ("fp64-thread", pse.PSE_FP64_PLAIN, pse.PSE_THREAD_PER_TET),
+    ("fp32-thread", pse.PSE_FP32_FP64ACC, pse.PSE_THREAD_PER_TET),
+    ("fp32-warp", pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_1612_09491_gb300 import build
+    build.build()
+    pse._lib.load()
+    yield
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def gpu_lattice(pos, n, g, prec, sched, **kw):
+    out = pse.deposit_uniform(dev(pos), n, g, precision=prec, schedule=sched, **kw)
+    if isinstance(out, tuple):
+        return out[0].cpu().numpy(), out[1]
+    return out.cpu().numpy()
+
+
+def gpu_tets(verts, mass, g, prec, sched, **kw):
+    out = pse.deposit_tets(dev(np.asarray(verts, np.float32)), dev(np.asarray(mass, np.float64)), g,
+                           precision=prec, schedule=sched, **kw)
+    if isinstance(out, tuple):
+        return out[0].cpu().numpy(), out[1]
+    return out.cpu().numpy()
+
+
+def tol_for(prec):
+    return TOL64 if prec == pse.PSE_FP64_PLAIN else TOL32
+
+
+# ------------------------------------------------------------ closed forms --
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_kuhn_simplex(name, prec, sched):
+    tet = np.array([[[0, 0, 0], [0, 0, 2], [0, 2, 2], [2, 2, 2]]], dtype=np.float32) / 2.0  # box 1, grid 2
+    m = gpu_tets(tet, [1.0], 2, prec, sched)
+    expect = np.zeros((2, 2, 2))
+    for (ix, iy, iz), v in {(0, 0, 0): 1 / 6, (0, 0, 1): 1 / 2, (0, 1, 1): 1 / 2, (1, 1, 1): 1 / 6}.items():
+        expect[iz, iy, ix] = v * 0.75  # mass 1 over volume 4/3 (cell units)
+    np.testing.assert_allclose(m, expect, rtol=0, atol=1e-7 if prec else 1e-15)
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+@pytest.mark.parametrize("n,g,offset", [(8, 8, 0.0), (8, 16, 0.0), (8, 4, 0.0), (16, 24, 0.0), (8, 5, 0.0),
+                                        (8, 16, 0.5), (16, 32, 0.25)])
+def test_undisplaced_lattice_uniform(name, prec, sched, n, g, offset):
+    """Every vertex on cell planes: the degenerate worst case; must stay exactly uniform."""
+    pos = lattice_positions(n, offset=offset)
+    m, st = gpu_lattice(pos, n, g, prec, sched, stats=True)
+    tol = 1e-13 if prec == pse.PSE_FP64_PLAIN else 1e-6
+    np.testing.assert_allclose(m, 1.0 / g ** 3, rtol=tol, atol=0)
+    assert st["tets"] == 6 * n ** 3
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_tet_inside_one_cell(name, prec, sched):
+    g = 8
+    h = 1.0 / g
+    tet = (np.array([3, 2, 5]) * h + h * np.array([[0.1, 0.2, 0.3], [0.9, 0.15, 0.2], [0.3, 0.8, 0.25],
+                                                   [0.4, 0.4, 0.95]]))[None]
+    m = gpu_tets(tet, [0.37], g, prec, sched)
+    assert m[5, 2, 3] == pytest.approx(0.37, rel=1e-15)
+    assert np.count_nonzero(m) == 1
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_cell_inside_tet(name, prec, sched):
+    g = 16
+    tet = np.array([[[0.05, 0.05, 0.05], [0.95, 0.1, 0.08], [0.1, 0.9, 0.1], [0.12, 0.11, 0.93]]], dtype=np.float32)
+    ref, _ = oracle.deposit_tets(tet.astype(np.float64), [1.0], g)
+    m = gpu_tets(tet, [1.0], g, prec, sched)
+    assert m[2, 2, 2] == pytest.approx(ref[2, 2, 2], rel=1e-12)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= tol_for(prec)
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_degenerate_tet_centroid_rule(name, prec, sched):
+    tet = np.array([[[0.1, 0.1, 0.3], [0.6, 0.1, 0.3], [0.1, 0.6, 0.3], [0.35, 0.35, 0.3]]], dtype=np.float32)
+    m, st = gpu_tets(tet, [0.5], 4, prec, sched, stats=True)
+    ref, _ = oracle.deposit_tets(tet.astype(np.float64), [0.5], 4)
+    np.testing.assert_array_equal(m, ref)
+    assert st["degenerate_tets"] == 1
+
+
+# ------------------------------------------------------------ vs the oracle --
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_random_dyadic_tets(name, prec, sched):
+    tets = random_dyadic_tets(300, seed=5, span=0.45, denom_bits=9, origin=0.05)
+    mass = np.random.default_rng(1).uniform(0.5, 2.0, len(tets))
+    ref, _ = oracle.deposit_tets(tets, mass, 16)
+    m = gpu_tets(tets, mass, 16, prec, sched)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= tol_for(prec), e
+    assert e["mass"] <= (1e-13 if prec == pse.PSE_FP64_PLAIN else MASS32), e
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_large_and_sliver_tets(name, prec, sched):
+    rng = np.random.default_rng(17)
+    big = rng.uniform(0.2, 0.8, size=(6, 4, 3))                      # spans ~20 cells per axis at g=32
+    base = rng.uniform(0.3, 0.7, size=(20, 1, 3))
+    sl = base + rng.normal(0, 0.02, size=(20, 4, 3)) * np.array([1, 1, 1e-3])  # flat slivers
+    tets = np.concatenate([big, sl]).astype(np.float32).astype(np.float64)
+    mass = np.ones(len(tets))
+    ref, _ = oracle.deposit_tets(tets, mass, 32)
+    m = gpu_tets(tets, mass, 32, prec, sched)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= tol_for(prec), e
+    assert e["mass"] <= (1e-13 if prec == pse.PSE_FP64_PLAIN else MASS32), e
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_config1_full(name, prec, sched):
+    """32^3 particles (196,608 tetrahedra), k^-2, rms 0.5 spacings, 64^3 grid: every cell."""
+    cfg = CONFIGS[1]
+    pos = config_positions(cfg)
+    ref, _ = oracle.deposit_lattice(pos, cfg.n, cfg.grid_n)
+    m, st = gpu_lattice(pos, cfg.n, cfg.grid_n, prec, sched, stats=True)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= tol_for(prec), e
+    assert e["mass"] <= (1e-13 if prec == pse.PSE_FP64_PLAIN else MASS32), e
+    assert st["tets"] == cfg.n_tets
+    assert abs(st["mass_in"] - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_shell_crossed_small(name, prec, sched):
+    """Strong shell crossing (rms 3 spacings, many inverted and sliver tetrahedra), 16^3 particles."""
+    n, g = 16, 48
+    pos = zeldovich_positions(n, -1.5, 3.0, seed=77)
+    ref, _ = oracle.deposit_lattice(pos, n, g)
+    m = gpu_lattice(pos, n, g, prec, sched)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= tol_for(prec), e
+    assert e["mass"] <= (1e-13 if prec == pse.PSE_FP64_PLAIN else MASS32), e
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_paper_jitter_input(name, prec, sched):
+    n, g = 16, 32
+    pos = jitter_positions(n, seed=3, amp=1.0)
+    ref, _ = oracle.deposit_lattice(pos, n, g)
+    m = gpu_lattice(pos, n, g, prec, sched)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= tol_for(prec), e
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_ragged_noncubic_lattice_and_grid(name, prec, sched):
+    """Row lengths that are not multiples of 32, anisotropic lattice and grid."""
+    n = (37, 6, 9)
+    rng = np.random.default_rng(4)
+    q = np.stack(np.meshgrid(*[np.arange(k) / k for k in n[::-1]], indexing="ij")[::-1], -1).reshape(-1, 3)
+    pos = np.mod(q + rng.normal(0, 0.3, q.shape) / np.array(n), 1.0).astype(np.float32)
+    g = (40, 12, 10)
+    ref, _ = oracle.deposit_lattice(pos, n, g)
+    m = gpu_lattice(pos, n, g, prec, sched)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= tol_for(prec), e
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_open_lattice_and_grid(name, prec, sched):
+    n, g = 12, 20
+    pos = zeldovich_positions(n, -2.0, 0.8, seed=9)
+    ref, rst = oracle.deposit_lattice(pos, n, g, periodic=False)
+    m, st = gpu_lattice(pos, n, g, prec, sched, periodic=False, stats=True)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= tol_for(prec), e
+    assert st["tets"] == 6 * (n - 1) ** 3
+    assert st["mass_dropped"] == pytest.approx(rst["lost_mass"], rel=1e-6, abs=1e-15)
+
+
+@pytest.mark.parametrize("name,prec,sched", PATHS)
+def test_cube_subset_and_accumulate(name, prec, sched):
+    n, g = 16, 32
+    pos = zeldovich_positions(n, -2.0, 1.0, seed=12)
+    ids = np.random.default_rng(2).permutation(n ** 3)
+    a_ids, b_ids = np.sort(ids[: n ** 3 // 3]), np.sort(ids[n ** 3 // 3:])
+    ref_a, _ = oracle.deposit_lattice(pos, n, g, cube_ids=a_ids)
+    ref, _ = oracle.deposit_lattice(pos, n, g)
+    dpos = dev(pos)
+    out = pse.deposit_uniform(dpos, n, g, precision=prec, schedule=sched, cube_ids=dev(a_ids))
+    e = cell_errors(out.cpu().numpy(), ref_a)
+    assert e["max_rel"] <= tol_for(prec), e
+    pse.deposit_uniform(dpos, n, g, precision=prec, schedule=sched, cube_ids=dev(b_ids), out=out, accumulate=True)
+    e = cell_errors(out.cpu().numpy(), ref)
+    assert e["max_rel"] <= tol_for(prec), e
+
+
+def test_empty_inputs():
+    out = pse.deposit_tets(torch.zeros((0, 4, 3), dtype=torch.float32, device="cuda"),
+                           torch.zeros((0,), dtype=torch.float64, device="cuda"), 8)
+    assert float(out.abs().sum()) == 0.0
+    out = pse.deposit_uniform(dev(lattice_positions(4)), 4, 4, cube_ids=torch.zeros((0,), dtype=torch.int64,
+                                                                                      device="cuda"))
+    assert float(out.abs().sum()) == 0.0
+
+
+def test_bad_cube_id_is_reported_not_read():
+    pos = dev(lattice_positions(4))
+    with pytest.raises(pse.PseError) as ei:
+        pse.deposit_uniform(pos, 4, 8, cube_ids=dev(np.array([0, 5, 64, 3], np.int64)), stats=True)
+    assert ei.value.code == -7
+
+
+def test_caller_workspace():
+    n, g = 8, 16
+    pos = dev(zeldovich_positions(n, -2.0, 1.0, seed=1))
+    ws = torch.empty(pse.workspace_size(), dtype=torch.uint8, device="cuda")
+    a = pse.deposit_uniform(pos, n, g, workspace=ws)
+    b = pse.deposit_uniform(pos, n, g)
+    e = cell_errors(a.cpu().numpy(), b.cpu().numpy())
+    assert e["max_rel"] <= 1e-12
+    with pytest.raises(pse.PseError):
+        pse.deposit_uniform(pos, n, g, workspace=ws[:8])
+
+
+def test_build_tets_matches_tessellation():
+    n = 6
+    pos = zeldovich_positions(n, -2.0, 1.0, seed=8)
+    vidx, vol = pse.build_tets_from_lagrangian_grid(dev(pos), n)
+    vidx, vol = vidx.cpu().numpy(), vol.cpu().numpy()
+    assert vidx.shape == (6 * n ** 3, 4)
+    for t in (0, 1, 5, 17, 6 * n ** 3 - 1):
+        tet = oracle.lattice_tet(pos, n, t // 6, t % 6)
+        assert abs(vol[t]) == pytest.approx(oracle.tet_volume(tet), rel=1e-5)
+        # the vertices are the particles named by vidx, unwrapped to the image nearest vertex 0
+        p = pos[vidx[t]].astype(np.float64)
+        d = p - p[0]
+        d -= np.floor(d + 0.5)
+        np.testing.assert_allclose(p[0] + d, tet, atol=1e-7)
+
+
+# ------------------------------------------------------------ full size ---
+def candidate_cubes(pos, n, cells, g):
+    """Cubes whose (unwrapped) corner bounding box touches any of the given cells."""
+    p = pos.reshape(n, n, n, 3).astype(np.float64)
+    corners = []
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                c = np.roll(p, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
+                d = c - p
+                d -= np.floor(d + 0.5)
+                corners.append(p + d)
+    cs = np.stack(corners, 0)  # [8, n, n, n, 3]
+    lo = np.floor(cs.min(0) * g).astype(np.int64)
+    ext = np.floor(cs.max(0) * g).astype(np.int64) - lo
+    sel = np.zeros((n, n, n), bool)
+    for c in cells:
+        # periodic containment: (c - lo) mod g <= extent on every axis
+        sel |= np.all(np.mod(np.asarray(c) - lo, g) <= ext, axis=-1)
+    kk, jj, ii = np.nonzero(sel)
+    return np.sort(ii + n * (jj + n * kk))
+
+
+def test_config2_full_size_sampled_cells():
+    """128^3 particles (12.6M tetrahedra) onto 256^3 in the bench's launch configuration;
+    64 random cells checked against the oracle run on every cube that can reach them."""
+    cfg = CONFIGS[2]
+    pos = config_positions(cfg)
+    m, st = gpu_lattice(pos, cfg.n, cfg.grid_n, pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE, stats=True)
+    assert st["tets"] == cfg.n_tets
+    assert abs(m.sum() - 1.0) <= MASS32
+    rng = np.random.default_rng(2024)
+    g = cfg.grid_n
+    cells = [tuple(int(x) for x in rng.integers(0, g, 3)) for _ in range(64)]
+    ids = candidate_cubes(pos, cfg.n, cells, g)
+    ref, _ = oracle.deposit_lattice(pos, cfg.n, g, cube_ids=ids, nthreads=4)
+    got = np.array([m[c[2], c[1], c[0]] for c in cells])
+    exp = np.array([ref[c[2], c[1], c[0]] for c in cells])
+    den = np.maximum(exp, 1e-3 / g ** 3)
+    assert np.max(np.abs(got - exp) / den) <= TOL32
+
+
+def test_config2_fp32_vs_fp64_gpu_all_cells():
+    """The FP32 warp path against the plain FP64 GPU path on every cell of config 2."""
+    cfg = CONFIGS[2]
+    dpos = dev(config_positions(cfg))
+    a = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, precision=pse.PSE_FP32_FP64ACC,
+                            schedule=pse.PSE_WARP_COOPERATIVE).cpu().numpy()
+    b = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, precision=pse.PSE_FP64_PLAIN,
+                            schedule=pse.PSE_THREAD_PER_TET).cpu().numpy()
+    e = cell_errors(a, b)
+    assert e["max_rel"] <= TOL32, e
+    assert e["mass"] <= MASS32, e
