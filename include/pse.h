@@ -101,7 +101,8 @@ typedef struct pse_deposit_opts {
     int32_t accumulate;      /* 0: the call overwrites the output; 1: it adds to it */
     int32_t mass_fixup;      /* FP32 path: 1 adds each tetrahedron's rounding residual m_t - sum(deposits)
                                 to the cell of its centroid, so total mass is conserved to float64 rounding */
-    const int64_t *d_cube_ids; /* nullable: deposit only these Lagrangian cubes (device int64 [n_cube_ids]) */
+    const int64_t *d_cube_ids; /* NULL: every cube; else deposit only these Lagrangian cubes (device int64
+                                  [n_cube_ids], each in [0, number of cubes); n_cube_ids may be 0) */
     int64_t n_cube_ids;
 } pse_deposit_opts;
 
@@ -119,7 +120,8 @@ typedef struct pse_deposit_stats {
 } pse_deposit_stats;
 
 typedef struct pse_tuning {
-    int32_t blocks_per_sm;   /* resident blocks per SM of the persistent kernels */
+    int32_t blocks_per_sm;   /* resident blocks per SM of the warp-cooperative kernel: 1 (no register
+                                cap) or 2 (128 registers per thread); <= 0: the built-in default */
     int32_t warps_per_block;
     int32_t bin_edges[7];    /* bbox-cell-count upper edges of bins 0..6 (bin 7 is the rest) */
     int32_t reserved;

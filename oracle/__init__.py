@@ -67,6 +67,14 @@ def lib():
             L.oracle_tet_cells.restype = ctypes.c_int64
             L.oracle_tet_volume.argtypes = [dp]
             L.oracle_tet_volume.restype = ctypes.c_double
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            L.oracle_build_octree.argtypes = [fp, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_double, i32p, ctypes.c_int64, dp, ctypes.c_int64, i64p]
+            L.oracle_build_octree.restype = ctypes.c_int64
+            L.oracle_deposit_octree.argtypes = [fp, i64p, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                                ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int64, dp, i64p,
+                                                ctypes.c_int64, ctypes.c_int, dp]
+            L.oracle_deposit_octree.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -171,3 +179,48 @@ def tet_cells(tet, h):
 def tet_volume(tet) -> float:
     t = np.ascontiguousarray(tet, dtype=np.float64).reshape(12)
     return lib().oracle_tet_volume(_ptr(t, ctypes.c_double))
+
+
+def build_octree(pos, n, bc: int, max_level: int, threshold_cells: float = 2.0, box: float = 1.0,
+                 periodic: bool = True):
+    """Exact-median octree (Sec. 4 structure, tetrahedron-size rule): (leaves [L,4] int32, nodes [K,7])."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(n, dtype=np.int64), (3,)))
+    cap, ncap = 4096, 8192
+    while True:
+        leaves = np.zeros((cap, 4), dtype=np.int32)
+        nodes = np.zeros((ncap, 7), dtype=np.float64)
+        nn = ctypes.c_int64(0)
+        cnt = lib().oracle_build_octree(_ptr(pos, ctypes.c_float), _ptr(n, ctypes.c_int64), box, int(periodic),
+                                        int(bc), int(max_level), float(threshold_cells),
+                                        _ptr(leaves, ctypes.c_int32), cap, _ptr(nodes, ctypes.c_double), ncap,
+                                        ctypes.byref(nn))
+        if cnt < 0:
+            raise RuntimeError(f"oracle_build_octree failed: {cnt}")
+        if cnt <= cap and nn.value <= ncap:
+            return leaves[:cnt].copy(), nodes[:nn.value].copy()
+        cap, ncap = max(cap, int(cnt)), max(ncap, int(nn.value))
+
+
+def deposit_octree(pos, n, leaves, bc: int, max_level: int, box: float = 1.0, periodic: bool = True,
+                   particle_mass: float | None = None, cube_ids=None, nthreads: int = 0):
+    """Leaf-block masses [n_leaves, bc, bc, bc] (x fastest within a block); returns (mass, stats)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(n, dtype=np.int64), (3,)))
+    leaves = np.ascontiguousarray(leaves, dtype=np.int32)
+    if particle_mass is None:
+        particle_mass = box ** 3 / float(np.prod(n))
+    nl = leaves.shape[0]
+    out = np.zeros(nl * bc ** 3, dtype=np.float64)
+    st = np.zeros(7, dtype=np.float64)
+    if cube_ids is not None:
+        cube_ids = np.ascontiguousarray(cube_ids, dtype=np.int64)
+        cptr, ncid = _ptr(cube_ids, ctypes.c_int64), cube_ids.size
+    else:
+        cptr, ncid = None, 0
+    rc = lib().oracle_deposit_octree(_ptr(pos, ctypes.c_float), _ptr(n, ctypes.c_int64), box, int(periodic),
+                                     particle_mass, int(bc), int(max_level), _ptr(leaves, ctypes.c_int32), nl,
+                                     _ptr(out, ctypes.c_double), cptr, ncid, int(nthreads), _ptr(st, ctypes.c_double))
+    if rc != 0:
+        raise RuntimeError(f"oracle_deposit_octree failed: {rc}")
+    return out.reshape(nl, bc, bc, bc), dict(zip(STAT_KEYS, st.tolist()))

@@ -539,3 +539,327 @@ double oracle_tet_volume(const double *tet12)
     memcpy(p, tet12, sizeof(p));
     return tet_abs_vol(p);
 }
+
+/* ------------------------------------------------------------------ */
+/* adaptive deposit grid: octree of cubic leaf blocks (Sec. 4)          */
+/* ------------------------------------------------------------------ */
+/*
+ * The root node is the whole box [0, box)^3 (periodic box; the paper's root is the
+ * tracers' bounding box).  A node at level l has side box/2^l and, if it is a
+ * leaf, carries a block of bc^3 cells of side h_l = box/(bc*2^l) (every leaf has
+ * the same cell count, Sec. 4).  Reading of the refinement rule used here (the
+ * paper refines on an overlap count; this build refines on tetrahedron size): a
+ * node is refined iff l < max_level and the median, over the tetrahedra whose
+ * vertex centroid lies in the node, of the tetrahedron's mean edge length is
+ * below threshold_cells * h_l.  A node without tetrahedra is a leaf.  The median
+ * is the exact lower median (element (count-1)/2 of the sorted values).
+ * Leaves are listed depth first, children in the order c = cx + 2 cy + 4 cz.
+ */
+
+typedef struct {
+    double *edge;     /* mean edge length of every tetrahedron (box units) */
+    double *cen;      /* vertex centroid folded into [0, box)^3 */
+    int64_t count;
+} tetsizes_t;
+
+static int cmp_double(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return (x < y) ? -1 : (x > y) ? 1 : 0;
+}
+
+typedef struct {
+    const tetsizes_t *ts;
+    double box, threshold;
+    int bc, max_level;
+    int32_t *leaves;
+    int64_t cap, n_leaves;
+    double *nodes;   /* optional per visited node: level, ix, iy, iz, count, median_cells, refined */
+    int64_t node_cap, n_nodes;
+} octbuild_t;
+
+static void build_node(octbuild_t *B, int level, int64_t ix, int64_t iy, int64_t iz, int64_t *idx, int64_t cnt)
+{
+    double side = B->box / (double)(1LL << level);
+    double h = side / B->bc;
+    double med = -1.0;
+    int refine = 0;
+    if (cnt > 0) {
+        double *v = (double *)malloc((size_t)cnt * sizeof(double));
+        for (int64_t i = 0; i < cnt; ++i) v[i] = B->ts->edge[idx[i]];
+        qsort(v, (size_t)cnt, sizeof(double), cmp_double);
+        med = v[(cnt - 1) / 2];
+        free(v);
+        refine = (level < B->max_level) && (med < B->threshold * h);
+    }
+    if (B->nodes && B->n_nodes < B->node_cap) {
+        double *o = B->nodes + 7 * B->n_nodes;
+        o[0] = level; o[1] = (double)ix; o[2] = (double)iy; o[3] = (double)iz;
+        o[4] = (double)cnt; o[5] = (med >= 0) ? med / h : -1.0; o[6] = refine;
+    }
+    B->n_nodes++;
+    if (!refine) {
+        if (B->n_leaves < B->cap) {
+            int32_t *o = B->leaves + 4 * B->n_leaves;
+            o[0] = level; o[1] = (int32_t)ix; o[2] = (int32_t)iy; o[3] = (int32_t)iz;
+        }
+        B->n_leaves++;
+        return;
+    }
+    /* partition the tetrahedra among the 8 children by centroid */
+    double half = side * 0.5;
+    int64_t *part[8];
+    int64_t pc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int c = 0; c < 8; ++c) part[c] = (int64_t *)malloc((size_t)(cnt > 0 ? cnt : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < cnt; ++i) {
+        const double *x = B->ts->cen + 3 * idx[i];
+        int cx = x[0] >= ix * side + half, cy = x[1] >= iy * side + half, cz = x[2] >= iz * side + half;
+        int c = cx + 2 * cy + 4 * cz;
+        part[c][pc[c]++] = idx[i];
+    }
+    for (int c = 0; c < 8; ++c) {
+        build_node(B, level + 1, 2 * ix + (c & 1), 2 * iy + ((c >> 1) & 1), 2 * iz + (c >> 2), part[c], pc[c]);
+        free(part[c]);
+    }
+}
+
+/* returns the number of leaves (may exceed cap: call again with a larger buffer), or < 0 */
+int64_t oracle_build_octree(const float *pos, const int64_t n[3], double box, int periodic, int bc, int max_level,
+                            double threshold_cells, int32_t *leaves_out, int64_t cap, double *nodes_out,
+                            int64_t node_cap, int64_t *n_nodes_out)
+{
+    if (!pos || !n || bc < 1 || max_level < 0 || max_level > 12 || !(box > 0)) return OR_ERR_ARG;
+    int64_t ncube = n_cubes_of(n, periodic);
+    tetsizes_t ts;
+    ts.count = 6 * ncube;
+    ts.edge = (double *)malloc((size_t)ts.count * sizeof(double));
+    ts.cen = (double *)malloc((size_t)ts.count * 3 * sizeof(double));
+    int64_t *idx = (int64_t *)malloc((size_t)ts.count * sizeof(int64_t));
+    if (!ts.edge || !ts.cen || !idx) { free(ts.edge); free(ts.cen); free(idx); return OR_ERR_MEM; }
+    for (int64_t q = 0; q < ncube; ++q) {
+        int64_t i, j, k;
+        cube_ijk(q, n, periodic, &i, &j, &k);
+        for (int s = 0; s < 6; ++s) {
+            double p[4][3];
+            lattice_tet(pos, n, box, periodic, i, j, k, s, p);
+            int64_t t = 6 * q + s;
+            double e = 0.0;
+            for (int a = 0; a < 4; ++a)
+                for (int b = a + 1; b < 4; ++b) {
+                    double d0 = p[b][0] - p[a][0], d1 = p[b][1] - p[a][1], d2 = p[b][2] - p[a][2];
+                    e += sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+                }
+            ts.edge[t] = e / 6.0;
+            for (int a = 0; a < 3; ++a) {
+                double c = 0.25 * (p[0][a] + p[1][a] + p[2][a] + p[3][a]);
+                c -= box * floor(c / box);
+                if (c >= box) c = 0.0;
+                ts.cen[3 * t + a] = c;
+            }
+            idx[t] = t;
+        }
+    }
+    octbuild_t B;
+    B.ts = &ts; B.box = box; B.threshold = threshold_cells; B.bc = bc; B.max_level = max_level;
+    B.leaves = leaves_out; B.cap = leaves_out ? cap : 0; B.n_leaves = 0;
+    B.nodes = nodes_out; B.node_cap = nodes_out ? node_cap : 0; B.n_nodes = 0;
+    build_node(&B, 0, 0, 0, 0, idx, ts.count);
+    free(ts.edge); free(ts.cen); free(idx);
+    if (n_nodes_out) *n_nodes_out = B.n_nodes;
+    return B.n_leaves;
+}
+
+/* ---- deposit onto the leaf blocks ---- */
+
+typedef struct {
+    double box;
+    int periodic, bc, max_level;
+    int64_t fine;          /* 2^max_level finest nodes per axis */
+    int32_t *fine_map;     /* leaf id of every finest node, x fastest */
+    const int32_t *leaves; /* [n_leaves][4] */
+    int64_t n_leaves;
+} octree_t;
+
+static int make_fine_map(octree_t *T)
+{
+    int64_t F = T->fine, nf = F * F * F;
+    T->fine_map = (int32_t *)malloc((size_t)nf * sizeof(int32_t));
+    if (!T->fine_map) return OR_ERR_MEM;
+    for (int64_t i = 0; i < nf; ++i) T->fine_map[i] = -1;
+    for (int64_t l = 0; l < T->n_leaves; ++l) {
+        const int32_t *L = T->leaves + 4 * l;
+        if (L[0] < 0 || L[0] > T->max_level) return OR_ERR_ARG;
+        int64_t span = 1LL << (T->max_level - L[0]);
+        for (int a = 1; a < 4; ++a)
+            if (L[a] < 0 || L[a] >= (1LL << L[0])) return OR_ERR_ARG;
+        for (int64_t z = L[3] * span; z < (L[3] + 1) * span; ++z)
+            for (int64_t y = L[2] * span; y < (L[2] + 1) * span; ++y)
+                for (int64_t x = L[1] * span; x < (L[1] + 1) * span; ++x) {
+                    int32_t *m = &T->fine_map[x + F * (y + F * z)];
+                    if (*m != -1) return OR_ERR_ARG; /* overlapping leaves */
+                    *m = (int32_t)l;
+                }
+    }
+    for (int64_t i = 0; i < nf; ++i)
+        if (T->fine_map[i] < 0) return OR_ERR_ARG; /* leaves do not tile the box */
+    return OR_OK;
+}
+
+static void deposit_one_tet_octree(const double p[4][3], double m_t, const octree_t *T, double *mass, ostats_t *st)
+{
+    const double box = T->box;
+    const int64_t F = T->fine;
+    const double df = box / (double)F;
+    const int64_t bc = T->bc, bc3 = bc * bc * bc;
+    st->tets += 1;
+    double vol = tet_abs_vol(p);
+    if (vol == 0.0) { /* degenerate: the cell that contains the vertex centroid */
+        double c[3];
+        int64_t f[3], k[3];
+        for (int a = 0; a < 3; ++a) {
+            c[a] = 0.25 * (p[0][a] + p[1][a] + p[2][a] + p[3][a]);
+            int64_t fu = (int64_t)floor(c[a] / df);
+            f[a] = fold(fu, F);
+            k[a] = (fu - f[a]) / F;
+        }
+        st->degenerate_tets += 1;
+        if (!T->periodic && (k[0] || k[1] || k[2])) { st->lost_mass += m_t; return; }
+        int32_t leaf = T->fine_map[f[0] + F * (f[1] + F * f[2])];
+        const int32_t *L = T->leaves + 4 * leaf;
+        double side = box / (double)(1LL << L[0]), h = side / bc;
+        int64_t cc[3];
+        for (int a = 0; a < 3; ++a) {
+            double lo = L[1 + a] * side + k[a] * box;
+            cc[a] = (int64_t)floor((c[a] - lo) / h);
+            if (cc[a] < 0) cc[a] = 0;
+            if (cc[a] >= bc) cc[a] = bc - 1;
+        }
+        mass[leaf * bc3 + cc[0] + bc * (cc[1] + bc * cc[2])] += m_t;
+        return;
+    }
+    double rho = m_t / vol;
+    double mn[3], mx[3];
+    int64_t f0[3], f1[3];
+    for (int a = 0; a < 3; ++a) {
+        mn[a] = mx[a] = p[0][a];
+        for (int v = 1; v < 4; ++v) { mn[a] = fmin(mn[a], p[v][a]); mx[a] = fmax(mx[a], p[v][a]); }
+        f0[a] = (int64_t)floor(mn[a] / df);
+        f1[a] = (int64_t)floor(mx[a] / df);
+    }
+    /* distinct (leaf, periodic image) pairs touched by the bounding box */
+    int64_t keys[512][4];
+    int nk = 0;
+    for (int64_t fz = f0[2]; fz <= f1[2]; ++fz)
+        for (int64_t fy = f0[1]; fy <= f1[1]; ++fy)
+            for (int64_t fx = f0[0]; fx <= f1[0]; ++fx) {
+                int64_t g[3] = {fold(fx, F), fold(fy, F), fold(fz, F)};
+                int64_t k[3] = {(fx - g[0]) / F, (fy - g[1]) / F, (fz - g[2]) / F};
+                if (!T->periodic && (k[0] || k[1] || k[2])) continue;
+                int64_t leaf = T->fine_map[g[0] + F * (g[1] + F * g[2])];
+                int dup = 0;
+                for (int q = 0; q < nk && !dup; ++q)
+                    dup = keys[q][0] == leaf && keys[q][1] == k[0] && keys[q][2] == k[1] && keys[q][3] == k[2];
+                if (!dup && nk < 512) {
+                    keys[nk][0] = leaf; keys[nk][1] = k[0]; keys[nk][2] = k[1]; keys[nk][3] = k[2];
+                    ++nk;
+                }
+            }
+    double deposited = 0.0;
+    for (int q = 0; q < nk; ++q) {
+        const int32_t *L = T->leaves + 4 * keys[q][0];
+        double side = box / (double)(1LL << L[0]), h = side / bc;
+        double lo[3];
+        int64_t c0[3], c1[3];
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = L[1 + a] * side + keys[q][1 + a] * box;
+            c0[a] = (int64_t)floor((mn[a] - lo[a]) / h);
+            c1[a] = (int64_t)floor((mx[a] - lo[a]) / h);
+            if (c0[a] < 0) c0[a] = 0;
+            if (c1[a] > bc - 1) c1[a] = bc - 1;
+        }
+        double *blk = mass + keys[q][0] * bc3;
+        for (int64_t cz = c0[2]; cz <= c1[2]; ++cz)
+            for (int64_t cy = c0[1]; cy <= c1[1]; ++cy)
+                for (int64_t cx = c0[0]; cx <= c1[0]; ++cx) {
+                    double clo[3] = {lo[0] + cx * h, lo[1] + cy * h, lo[2] + cz * h};
+                    double chi[3] = {lo[0] + (cx + 1) * h, lo[1] + (cy + 1) * h, lo[2] + (cz + 1) * h};
+                    st->bbox_cells += 1;
+                    double v;
+                    switch (classify(p, clo, chi)) {
+                    case CLS_OUTSIDE: v = 0.0; break;
+                    case CLS_TET_IN_CELL: v = vol; break;
+                    case CLS_CELL_IN_TET: v = h * h * h; break;
+                    default:
+                        st->partial_cells += 1;
+                        v = tet_box_volume(p, clo, chi);
+                        break;
+                    }
+                    if (v > 0.0) {
+                        st->overlapped_cells += 1;
+                        blk[cx + bc * (cy + bc * cz)] += rho * v;
+                        deposited += rho * v;
+                    }
+                }
+    }
+    if (!T->periodic) st->lost_mass += m_t - deposited;
+}
+
+/* leaf_mass [n_leaves * bc^3]: block of leaf l at l*bc^3, cells x fastest */
+int oracle_deposit_octree(const float *pos, const int64_t n[3], double box, int periodic, double particle_mass,
+                          int bc, int max_level, const int32_t *leaves, int64_t n_leaves, double *leaf_mass,
+                          const int64_t *cube_ids, int64_t n_cube_ids, int nthreads, double *stats_out)
+{
+    if (!pos || !n || !leaves || !leaf_mass || bc < 1 || max_level < 0 || max_level > 10 || !(box > 0))
+        return OR_ERR_ARG;
+    octree_t T;
+    T.box = box; T.periodic = periodic; T.bc = bc; T.max_level = max_level;
+    T.fine = 1LL << max_level; T.leaves = leaves; T.n_leaves = n_leaves; T.fine_map = NULL;
+    int rc = make_fine_map(&T);
+    if (rc != OR_OK) { free(T.fine_map); return rc; }
+    int64_t ncell = n_leaves * (int64_t)bc * bc * bc;
+    int64_t ncube = cube_ids ? n_cube_ids : n_cubes_of(n, periodic);
+    int nt = pick_threads(nthreads);
+    double **priv = (double **)calloc((size_t)nt, sizeof(double *));
+    ostats_t *pst = (ostats_t *)calloc((size_t)nt, sizeof(ostats_t));
+    if (!priv || !pst) { free(priv); free(pst); free(T.fine_map); return OR_ERR_MEM; }
+    for (int t = 0; t < nt; ++t) {
+        priv[t] = (double *)calloc((size_t)ncell, sizeof(double));
+        if (!priv[t]) {
+            for (int u = 0; u < t; ++u) free(priv[u]);
+            free(priv); free(pst); free(T.fine_map);
+            return OR_ERR_MEM;
+        }
+    }
+    double m_t = particle_mass / 6.0;
+#pragma omp parallel for num_threads(nt) schedule(static)
+    for (int64_t q = 0; q < ncube; ++q) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        int64_t cube = cube_ids ? cube_ids[q] : q;
+        int64_t i, j, k;
+        cube_ijk(cube, n, periodic, &i, &j, &k);
+        for (int s = 0; s < 6; ++s) {
+            double p[4][3];
+            lattice_tet(pos, n, box, periodic, i, j, k, s, p);
+            deposit_one_tet_octree(p, m_t, &T, priv[tid], &pst[tid]);
+        }
+    }
+    memset(leaf_mass, 0, (size_t)ncell * sizeof(double));
+    ostats_t tot = {0, 0, 0, 0, 0, 0};
+    for (int t = 0; t < nt; ++t) {
+        for (int64_t c = 0; c < ncell; ++c) leaf_mass[c] += priv[t][c];
+        free(priv[t]);
+        tot.tets += pst[t].tets; tot.bbox_cells += pst[t].bbox_cells;
+        tot.overlapped_cells += pst[t].overlapped_cells; tot.partial_cells += pst[t].partial_cells;
+        tot.degenerate_tets += pst[t].degenerate_tets; tot.lost_mass += pst[t].lost_mass;
+    }
+    free(priv); free(pst); free(T.fine_map);
+    if (stats_out) {
+        stats_out[0] = tot.tets; stats_out[1] = tot.bbox_cells; stats_out[2] = tot.overlapped_cells;
+        stats_out[3] = tot.partial_cells; stats_out[4] = tot.degenerate_tets; stats_out[5] = tot.lost_mass;
+        stats_out[6] = nt;
+    }
+    return OR_OK;
+}

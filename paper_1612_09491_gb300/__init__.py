@@ -23,6 +23,9 @@ __all__ = ["build_tets_from_lagrangian_grid", "deposit_uniform", "deposit_tets",
            "abi_version", "lattice", "opts"]
 
 
+_EMPTY_SENTINEL = 16  # non-NULL, never dereferenced (n_cube_ids == 0)
+
+
 def _torch():
     import torch
     return torch
@@ -58,16 +61,27 @@ def lattice(n, box: float = 1.0, periodic: bool = True, particle_mass: float | N
     return lat
 
 
+_keep = []  # tuning blocks referenced by option structs during a call
+
+
 def opts(precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
-         accumulate: bool = False, mass_fixup: bool = True, cube_ids=None) -> _lib.DepositOpts:
+         accumulate: bool = False, mass_fixup: bool = True, cube_ids=None, tuning=None) -> _lib.DepositOpts:
     o = _lib.DepositOpts()
+    if tuning is not None:
+        tu = _lib.Tuning()
+        tu.blocks_per_sm = int(tuning.get("blocks_per_sm", 0))
+        tu.warps_per_block = int(tuning.get("warps_per_block", 0))
+        _keep[:] = [tu]
+        o.tuning = ctypes.cast(ctypes.pointer(tu), ctypes.c_void_p).value
     o.precision = precision
     o.schedule = schedule
     o.guard_eps = guard_eps
     o.accumulate = 1 if accumulate else 0
     o.mass_fixup = 1 if mass_fixup else 0
     if cube_ids is not None:
-        o.d_cube_ids = _dev_ptr(cube_ids, _torch().int64, "cube_ids").value
+        _dev_ptr(cube_ids, _torch().int64, "cube_ids")
+        # an empty subset still needs a non-NULL pointer (NULL means "every cube"); it is never read
+        o.d_cube_ids = cube_ids.data_ptr() if cube_ids.numel() > 0 else _EMPTY_SENTINEL
         o.n_cube_ids = cube_ids.numel()
     return o
 
@@ -80,7 +94,7 @@ def _grid3(grid_n):
 def deposit_uniform(pos, n, grid_n, *, box: float = 1.0, periodic: bool = True, particle_mass=None, out=None,
                     precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
                     accumulate: bool = False, mass_fixup: bool = True, cube_ids=None, stats: bool = False,
-                    workspace=None, stream=None):
+                    workspace=None, stream=None, tuning=None):
     """pse_deposit_uniform: cell masses float64 [g2, g1, g0] (x fastest)."""
     torch = _torch()
     L = _lib.load()
@@ -88,7 +102,7 @@ def deposit_uniform(pos, n, grid_n, *, box: float = 1.0, periodic: bool = True, 
     g3, g = _grid3(grid_n)
     if out is None:
         out = torch.empty((g[2], g[1], g[0]), dtype=torch.float64, device=pos.device)
-    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, cube_ids)
+    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, cube_ids, tuning)
     st = _lib.DepositStats() if stats else None
     ws_ptr, ws_bytes = (ctypes.c_void_p(None), 0) if workspace is None else \
         (_dev_ptr(workspace, torch.uint8, "workspace"), workspace.numel())

@@ -68,6 +68,11 @@ class DepositStats(ctypes.Structure):
         return d
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
+                ("bin_edges", ctypes.c_int32 * 7), ("reserved", ctypes.c_int32)]
+
+
 class PseError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"pse error {code}: {msg}")

@@ -44,14 +44,20 @@ pse_deposit_opts default_opts()
     return o;
 }
 
-// FP32 guard: a tetrahedron whose conditioning estimate kappa (surface * longest edge /
-// |6V|) times the float32 unit roundoff exceeds guard_eps is clipped in float64.
-constexpr double kDefaultGuardEps = 2.0e-5;
+// FP32 guard: a tetrahedron whose conditioning estimate kappa (total face area x longest
+// edge / |6V|; about 8 for an undistorted Kuhn tetrahedron) exceeds kappa_max is clipped
+// in float64.  kappa_max = 6.4e6 * guard_eps: measured on shell-crossed Zel'dovich and
+// jittered lattices, FP32 clips of tetrahedra below this bound keep the per-cell error
+// (relative, floored at 1e-3 of the mean cell mass) below about guard_eps.
+constexpr double kDefaultGuardEps = 1.0e-5;
+
+// resident blocks per SM of the warp-cooperative kernel (1: no register cap; 2: 128 registers)
+constexpr int kDefaultBlocksPerSm = 1;
 
 float kappa_limit(double guard_eps)
 {
     const double g = guard_eps > 0.0 ? guard_eps : kDefaultGuardEps;
-    return (float)(g / (double)FLT_EPSILON);
+    return (float)(6.4e6 * g);
 }
 
 struct WsLease {
@@ -140,7 +146,9 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
             e = pse::launch_thread_per_tet(p, o.precision == PSE_FP64_PLAIN, stats, st);
         } else {
             p.n_items = (p.src == pse::SRC_LATTICE) ? ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2] : (p.n_units + 31) / 32;
-            e = pse::launch_warp_coop(p, stats, st);
+            const pse_tuning *tu = static_cast<const pse_tuning *>(o.tuning);
+            const int bps = (tu && tu->blocks_per_sm > 0) ? tu->blocks_per_sm : kDefaultBlocksPerSm;
+            e = pse::launch_warp_coop(p, stats, bps, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
     }

@@ -271,10 +271,6 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
         }
         const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
         if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
-        if (P.periodic && (ts.dim[0] > P.g[0] || ts.dim[1] > P.g[1] || ts.dim[2] > P.g[2])) {
-            set_error(P.ws, 1, (int)(t & 0x7fffffff));
-            continue;
-        }
         if (ncell == 1) {
             if (!deposit_cell(P, base[0] + ts.lo[0], base[1] + ts.lo[1], base[2] + ts.lo[2], m_t) && STATS)
                 cnt.dropped += m_t;
@@ -282,6 +278,9 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
             continue;
         }
         const double rho = 6.0 * m_t / ts.vol6;
+        // FP32 guard: ill-conditioned tetrahedra are clipped in float64
+        const bool g64 = (sizeof(T) == 4) && !(ts.kappa <= P.kappa_max);
+        double dsum = 0.0;
         for (int iz = 0; iz < ts.dim[2]; ++iz)
             for (int iy = 0; iy < ts.dim[1]; ++iy)
                 for (int ix = 0; ix < ts.dim[0]; ++ix) {
@@ -293,20 +292,38 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                         if (STATS) cnt.u[ST_INSIDE_CELLS]++;
                     } else if (cls == CELL_PARTIAL) {
                         P3<T> p[4];
-                        T e[4];
 #pragma unroll
                         for (int q = 0; q < 4; ++q) p[q] = mk<T>(ts.v[q].x - (T)cx, ts.v[q].y - (T)cy, ts.v[q].z - (T)cz);
-#pragma unroll
-                        for (int f = 0; f < 4; ++f) e[f] = dot(ts.n[f], (f == 0) ? p[1] : p[0]);
-                        vol = (double)overlap_volume<T>(p, ts.n, e, ts.inv_n2);
+                        if constexpr (sizeof(T) == 4) {
+                            if (g64) {
+                                vol = overlap_volume_fp64(p);
+                                if (STATS) cnt.u[ST_FP64_REDOS]++;
+                            } else {
+                                T err;
+                                vol = (double)overlap_volume<T>(p, ts.n, ts.lx, ts.ly, err);
+                            }
+                        } else {
+                            T err;
+                            vol = (double)overlap_volume<T>(p, ts.n, ts.lx, ts.ly, err);
+                        }
                         if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
                     }
                     if (vol > 0.0) {
-                        if (!deposit_cell(P, (int64_t)base[0] + cx, (int64_t)base[1] + cy, (int64_t)base[2] + cz,
-                                          rho * vol) && STATS)
-                            cnt.dropped += rho * vol;
+                        const double m = rho * vol;
+                        dsum += m;
+                        if (!deposit_cell(P, (int64_t)base[0] + cx, (int64_t)base[1] + cy, (int64_t)base[2] + cz, m) &&
+                            STATS)
+                            cnt.dropped += m;
                     }
                 }
+        // FP32 path: the rounding residual of this tetrahedron's mass goes to its centroid cell
+        if (sizeof(T) == 4 && P.fixup && m_t != dsum) {
+            int c[3];
+            centroid_cell(ts.v, c);
+            if (!deposit_cell(P, (int64_t)base[0] + c[0], (int64_t)base[1] + c[1], (int64_t)base[2] + c[2], m_t - dsum) &&
+                STATS)
+                cnt.dropped += m_t - dsum;
+        }
     }
     if (STATS) cnt.flush(P.ws);
 }
@@ -320,6 +337,7 @@ struct WarpSmem {
     float e[4][32];
     float pos[4][32];
     float neg[4][32];
+    float lx[32], ly[32];  // reference-plane slopes
     int lo[3][32];
     int dim[3][32];
     int base[3][32];
@@ -327,8 +345,17 @@ struct WarpSmem {
     double dsum[32];      // FP64 sum of what each tetrahedron deposited
     int start[32];        // exclusive prefix of the pair counts
     int guard[32];        // 1: clip this tetrahedron in float64
-    unsigned q[64];       // queued partial pairs: (local pair index << 5) | tetrahedron
+    unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
 };
+
+constexpr int kQBits = 19;  // per-axis cell offset bits in a queue entry
+constexpr unsigned long long kQMask = (1ull << kQBits) - 1;
+
+__device__ __forceinline__ unsigned long long q_pack(int t, int ix, int iy, int iz)
+{
+    return (unsigned long long)t | ((unsigned long long)ix << 5) | ((unsigned long long)iy << (5 + kQBits)) |
+           ((unsigned long long)iz << (5 + 2 * kQBits));
+}
 
 __device__ __forceinline__ void decompose(int local, int dx, int dy, int &ix, int &iy, int &iz)
 {
@@ -339,16 +366,45 @@ __device__ __forceinline__ void decompose(int local, int dx, int dy, int &ix, in
     ix = r - iy * dx;
 }
 
+// Adds each lane's v into S->dsum[key] when the lanes holding the same key are
+// contiguous (key < 0: no contribution): a segmented reduction to the first lane of
+// each run, which then updates the shared sum without atomics.
+__device__ __forceinline__ void segmented_add(WarpSmem *S, int lane, int key, double v)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_down_sync(kFull, v, o);
+        const int k2 = __shfl_down_sync(kFull, key, o);
+        if (lane + o < 32 && k2 == key) v += y;
+    }
+    const int kp = __shfl_up_sync(kFull, key, 1);
+    if (key >= 0 && (lane == 0 || kp != key)) S->dsum[key] += v;
+}
+
+// The float64 redo of a guarded clip, kept out of line so that the FP32 hot loop
+// stays small; vertices passed by value (cell frame, positively oriented).
+__device__ __noinline__ double redo_fp64(float x0, float y0, float z0, float x1, float y1, float z1, float x2,
+                                         float y2, float z2, float x3, float y3, float z3)
+{
+    P3<float> p[4];
+    p[0] = mk<float>(x0, y0, z0);
+    p[1] = mk<float>(x1, y1, z1);
+    p[2] = mk<float>(x2, y2, z2);
+    p[3] = mk<float>(x3, y3, z3);
+    return overlap_volume_fp64(p);
+}
+
 template <bool STATS>
 __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
 {
+    int key = -1;
+    double m = 0.0;
     if (lane < count) {
-        const unsigned ent = S->q[lane];
+        const unsigned long long ent = S->q[lane];
         const int t = (int)(ent & 31u);
-        const int local = (int)(ent >> 5);
-        int ix, iy, iz;
-        decompose(local, S->dim[0][t], S->dim[1][t], ix, iy, iz);
-        const int cx = S->lo[0][t] + ix, cy = S->lo[1][t] + iy, cz = S->lo[2][t] + iz;
+        const int cx = S->lo[0][t] + (int)((ent >> 5) & kQMask);
+        const int cy = S->lo[1][t] + (int)((ent >> (5 + kQBits)) & kQMask);
+        const int cz = S->lo[2][t] + (int)((ent >> (5 + 2 * kQBits)) & kQMask);
         const float fx = (float)cx, fy = (float)cy, fz = (float)cz;
         P3<float> p[4];
 #pragma unroll
@@ -357,47 +413,30 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
         double vol;
         if (!S->guard[t]) {
             P3<float> n[4];
-            float e[4], i2[4];
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
-                e[f] = dot(n[f], (f == 0) ? p[1] : p[0]);
-                const float nn = dot(n[f], n[f]);
-                i2[f] = nn > 0.f ? __frcp_rn(nn) : 0.f;
-            }
-            vol = (double)overlap_volume<float>(p, n, e, i2);
+            for (int f = 0; f < 4; ++f) n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
+            float err;
+            vol = (double)overlap_volume<float>(p, n, S->lx[t], S->ly[t], err);
         } else {
-            P3<double> pd[4], nd[4];
-            double ed[4], i2d[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) pd[q] = mk<double>(p[q].x, p[q].y, p[q].z);
-#pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                int ia, ib, ic;
-                face_vertices(f, ia, ib, ic);
-                const P3<double> a = pick4(pd, ia), b = pick4(pd, ib), c = pick4(pd, ic);
-                nd[f] = cross(sub(b, a), sub(c, a));
-                ed[f] = dot(nd[f], a);
-                const double nn = dot(nd[f], nd[f]);
-                i2d[f] = nn > 0.0 ? 1.0 / nn : 0.0;
-            }
-            vol = overlap_volume<double>(pd, nd, ed, i2d);
+            vol = redo_fp64(p[0].x, p[0].y, p[0].z, p[1].x, p[1].y, p[1].z, p[2].x, p[2].y, p[2].z, p[3].x, p[3].y,
+                            p[3].z);
             if (STATS) cnt.u[ST_FP64_REDOS]++;
         }
         if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
+        key = t;
         if (vol > 0.0) {
-            const double m = S->rho[t] * vol;
+            m = S->rho[t] * vol;
             if (!deposit_cell(P, (int64_t)S->base[0][t] + cx, (int64_t)S->base[1][t] + cy,
                               (int64_t)S->base[2][t] + cz, m) && STATS)
                 cnt.dropped += m;
-            atomicAdd(&S->dsum[t], m);
         }
     }
+    if (P.fixup) segmented_add(S, lane, key, m);
     __syncwarp();
 }
 
-template <bool STATS>
-__global__ void __launch_bounds__(256) k_warp_coop(const DepositParams P)
+template <bool STATS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
@@ -466,8 +505,6 @@ __global__ void __launch_bounds__(256) k_warp_coop(const DepositParams P)
                         STATS)
                         cnt.dropped += m_t;
                     if (STATS) cnt.u[ST_DEGENERATE]++;
-                } else if (P.periodic && (ts.dim[0] > P.g[0] || ts.dim[1] > P.g[1] || ts.dim[2] > P.g[2])) {
-                    set_error(P.ws, 1, lane);
                 } else if (ncell == 1) {
                     if (!deposit_cell(P, (int64_t)base[0] + ts.lo[0], (int64_t)base[1] + ts.lo[1],
                                       (int64_t)base[2] + ts.lo[2], m_t) && STATS)
@@ -498,7 +535,9 @@ __global__ void __launch_bounds__(256) k_warp_coop(const DepositParams P)
                         S->base[a][lane] = base[a];
                     }
                     S->rho[lane] = 6.0 * m_t / ts.vol6;
-                    S->guard[lane] = (ts.kappa > P.kappa_max) ? 1 : 0;
+                    S->lx[lane] = ts.lx;
+                    S->ly[lane] = ts.ly;
+                    S->guard[lane] = (ts.kappa <= P.kappa_max) ? 0 : 1;
                 }
             }
             // ---- 2. pair enumeration
@@ -516,7 +555,9 @@ __global__ void __launch_bounds__(256) k_warp_coop(const DepositParams P)
             for (int b0 = 0; b0 < total; b0 += 32) {
                 const int idx = b0 + lane;
                 bool partial = false;
-                unsigned ent = 0;
+                unsigned long long ent = 0;
+                int ikey = -1;
+                double im = 0.0;
                 if (idx < total) {
                     int t = 0;
 #pragma unroll
@@ -542,13 +583,15 @@ __global__ void __launch_bounds__(256) k_warp_coop(const DepositParams P)
                         if (!deposit_cell(P, (int64_t)S->base[0][t] + (int64_t)cx, (int64_t)S->base[1][t] + (int64_t)cy,
                                           (int64_t)S->base[2][t] + (int64_t)cz, m) && STATS)
                             cnt.dropped += m;
-                        atomicAdd(&S->dsum[t], m);
+                        ikey = t;
+                        im = m;
                         if (STATS) cnt.u[ST_INSIDE_CELLS]++;
                     } else if (cls == CELL_PARTIAL) {
                         partial = true;
-                        ent = ((unsigned)local << 5) | (unsigned)t;
+                        ent = q_pack(t, ix, iy, iz);
                     }
                 }
+                if (P.fixup && __any_sync(kFull, ikey >= 0)) segmented_add(S, lane, ikey, im);
                 const unsigned bal = __ballot_sync(kFull, partial);
                 if (partial) S->q[qn + __popc(bal & lt_mask)] = ent;
                 qn += __popc(bal);
@@ -662,19 +705,20 @@ cudaError_t launch_thread_per_tet(const DepositParams &p, bool fp64, bool stats,
     return cudaGetLastError();
 }
 
-cudaError_t launch_warp_coop(const DepositParams &p, bool stats, cudaStream_t st)
+cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st)
 {
     const int threads = 256;
     const size_t smem = sizeof(WarpSmem) * (threads / 32);
-    const void *k = stats ? (const void *)k_warp_coop<true> : (const void *)k_warp_coop<false>;
+    const int minb = (blocks_per_sm >= 2) ? 2 : 1;
+    const void *k = stats ? (minb == 2 ? (const void *)k_warp_coop<true, 2> : (const void *)k_warp_coop<true, 1>)
+                          : (minb == 2 ? (const void *)k_warp_coop<false, 2> : (const void *)k_warp_coop<false, 1>);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);
     const int64_t need = (p.n_items + 7) / 8;
     if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
-    if (stats) k_warp_coop<true><<<blocks, threads, smem, st>>>(p);
-    else k_warp_coop<false><<<blocks, threads, smem, st>>>(p);
-    return cudaGetLastError();
+    void *args[] = {const_cast<DepositParams *>(&p)};
+    return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
 }
 
 cudaError_t launch_build_tets(const float *pos, const int64_t n[3], const int64_t nc[3], int periodic, double box,

@@ -5,30 +5,41 @@
 // base cell; the clip works in the frame of one cell, where that cell is [0,1]^3.
 //
 // Overlap volume (the operation of Sec. 6.3, computed by a different method than
-// the paper's recursive split): for the cell C = [0,1)^3 = column x [0,1) with
-// column = [0,1)^2 in (x, y), take the field F = (0, 0, chi_col(x,y) clamp(z,0,1)),
-// whose divergence is the indicator of C.  Integrating along z over the convex
-// tetrahedron T (between its lower and upper surfaces) gives
+// the paper's recursive split).  For the cell C = [0,1)^3 = column x [0,1) with
+// column = [0,1)^2 in (x, y), take a field F = (0, 0, chi_col(x,y) clamp(z,0,1) - g(x,y))
+// with any g that does not depend on z: its divergence is the indicator of C.
+// Integrating along z over the convex tetrahedron T gives
 //
-//     vol(T ∩ C) = Σ_faces f of T  ∫_{F_f} chi_col(x,y) clamp(z,0,1) n_z dA
-//                = Σ_f  ∫∫_{proj_xy(F_f) ∩ column} clamp(z_f(x,y), 0, 1) dx dy  (signed by n_z)
+//   vol(T ∩ C) = Σ_faces f  ∫∫_{proj_xy(F_f) ∩ column} (clamp(z_f(x,y), 0, 1) - g(x,y)) dx dy
 //
-// so only the four face triangles of T are clipped, never the polytope T ∩ C.
-// Per face: Sutherland-Hodgman clips against x >= 0, x < 1, y >= 0, y < 1 and
-// z >= 0 on an edge list (the polygon stays a closed chain; every slot is a
-// compile-time register), then a split at z = 1: the part below contributes the
-// projected integral of z (a fan from an anchor o on the face plane,
-// Σ_edges ½ cross_xy(a-o, b-o) (z_o + z_a + z_b)/3), the part above contributes
-// its projected area.  Faces with n_z = 0 contribute nothing.
+// (signed by the sign of the face normal's z component), so only the four face
+// triangles of T are clipped, never the polytope T ∩ C.  g integrates to zero
+// over the closed surface; it is there for accuracy: g = l(x, y), the plane of
+// the tetrahedron's most horizontal face moved through its centroid, makes the
+// integrands of the large faces of a flat ("sliver") tetrahedron small instead
+// of O(1) numbers that cancel.
 //
+// Per face: Sutherland-Hodgman clips against the column's four sides on an edge
+// list (the polygon stays a closed chain; every slot is a compile-time register),
+// then splits at z = 0 and z = 1.  Each region integrates a linear function of
+// (x, y) by a fan from an anchor, Σ_edges ½ cross_xy(a-o, b-o) (f(o)+f(a)+f(b))/3:
+// below z = 0, f = 0 - l; above z = 1, f = 1 - l (anchor: the local origin, these
+// integrands are defined on the whole plane); between, f = z_f - l (anchor: the
+// local origin projected onto the face plane).
+//
+// The arithmetic runs in a local frame whose origin q is the tetrahedron's
+// centroid clamped into the cell and rounded to a multiple of 1/256, so the
+// cell planes stay exact and rounding is relative to the size of the pieces.
 // The result is a continuous function of the four vertices: a vertex or a face
 // lying exactly on a cell plane needs no tie rule (whichever side a tie goes,
 // the clipped polygon is the same, and anything lying in a plane x = const or
-// y = const has zero projected area), so rounding in near-degenerate
-// configurations costs rounding-sized errors only.
+// y = const has zero projected area), so near-degenerate configurations cost
+// rounding-sized errors only.  The clip also returns the sum of the magnitudes
+// of its terms, which bounds its rounding error (used by the FP32 guard).
 #pragma once
 
 #include <cstdint>
+#include <limits>
 #include <cuda_runtime.h>
 
 #ifndef PSE_HD
@@ -78,10 +89,28 @@ PSE_HD double fdiv(double a, double b) { return a / b; }
 PSE_HD float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 PSE_HD double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
+// products rounded on their own (never fused), so that cross_xy(u, u) is exactly 0
+PSE_HD float mul_rn(float a, float b)
+{
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+PSE_HD double mul_rn(double a, double b)
+{
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+
 template <class T>
 PSE_HD T cross_xy(const P3<T> &a, const P3<T> &b)
 {
-    return a.x * b.y - a.y * b.x;
+    return mul_rn(a.x, b.y) - mul_rn(a.y, b.x);
 }
 
 template <class T>
@@ -122,134 +151,217 @@ PSE_HD P3<T> pick4(const P3<T> (&p)[4], int i)
 }
 
 // ---------------------------------------------------------------------------
-// Sutherland-Hodgman clip of an edge-list polygon against one cell plane.
-// Slots [0, NE) hold the current edges (a -> b); the edge this clip creates on
-// the plane (exit -> entry) goes to slot NE.  Dropped edges collapse onto the
-// anchor o, which makes their fan contribution exactly zero.
+// Sutherland-Hodgman clip of an edge-list polygon against the plane x_AX = s,
+// keeping x_AX >= s (UP = false) or x_AX < s (UP = true).  Slots [0, NE) hold the
+// current edges (a -> b); the edge the clip creates on the plane (exit -> entry)
+// goes to slot NE.  Dropped edges collapse onto the local origin (zero length).
 // ---------------------------------------------------------------------------
 template <class T, int AX, bool UP, int NE>
-PSE_HD void clip_plane(P3<T> (&A)[9], P3<T> (&B)[9], const P3<T> &o, bool &crossed)
+PSE_HD void clip_plane(P3<T> (&A)[9], P3<T> (&B)[9], T s, T tol)
 {
-    P3<T> ex = o, en = o;
-    bool got = false;
+    const P3<T> z0 = mk<T>(T(0), T(0), T(0));
+    P3<T> ex = z0, en = z0;
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
+        // coordinates within rounding distance of the plane are put on it, so that a
+        // polygon that is convex up to rounding crosses the plane at most twice
+        if (fabs(get<AX>(A[k]) - s) <= tol) put<AX>(A[k], s);
+        if (fabs(get<AX>(B[k]) - s) <= tol) put<AX>(B[k], s);
         const T ca = get<AX>(A[k]), cb = get<AX>(B[k]);
-        const bool ia = UP ? (ca < T(1)) : (ca >= T(0));
-        const bool ib = UP ? (cb < T(1)) : (cb >= T(0));
+        const bool ia = UP ? (ca < s) : (ca >= s);
+        const bool ib = UP ? (cb < s) : (cb >= s);
         if (ia != ib) {
-            const T s = UP ? T(1) : T(0);
             const T t = fdiv(s - ca, cb - ca);
             P3<T> I = mk<T>(fmaT(t, B[k].x - A[k].x, A[k].x), fmaT(t, B[k].y - A[k].y, A[k].y),
                             fmaT(t, B[k].z - A[k].z, A[k].z));
             put<AX>(I, s);
             if (ia) { B[k] = I; ex = I; } else { A[k] = I; en = I; }
-            got = true;
         } else if (!ia) {
-            A[k] = o;
-            B[k] = o;
+            A[k] = z0;
+            B[k] = z0;
         }
     }
     A[NE] = ex;
     B[NE] = en;
-    crossed = got;
 }
 
 template <class T, int NE>
-PSE_HD void collapse_slot(P3<T> (&A)[9], P3<T> (&B)[9], const P3<T> &o)
+PSE_HD void collapse_slot(P3<T> (&A)[9], P3<T> (&B)[9])
 {
-    A[NE] = o;
-    B[NE] = o;
+    A[NE] = mk<T>(T(0), T(0), T(0));
+    B[NE] = A[NE];
 }
 
-// Split the edge-list polygon at z = 1: the part with z < 1 stays in slots [0, NE)
-// (its new edge on z = 1 goes to slot NE); the part with z >= 1 is not stored, its
-// doubled projected area about the column centre (½, ½) is returned.
-template <class T, int NE>
-PSE_HD T split_z1(P3<T> (&A)[9], P3<T> (&B)[9], const P3<T> &o)
+// Split the edge-list polygon at z = s.  The kept part (z >= s if KEEP_ABOVE, else
+// z < s) stays in slots [0, NE) with its new edge in slot NE; the other part is
+// integrated on the fly: returns 6 * ∫∫ (s - l(x,y)) dx dy over its projection
+// (fan from the local origin), l(x,y) = l0 + lx x + ly y.
+template <class T, int NE, bool KEEP_ABOVE>
+PSE_HD T split_z(P3<T> (&A)[9], P3<T> (&B)[9], T s, T tol, T l0, T lx, T ly)
 {
-    P3<T> ex = o, en = o;
+    const P3<T> z0 = mk<T>(T(0), T(0), T(0));
+    P3<T> ex = z0, en = z0;
     bool got = false;
-    T hi2 = T(0);
-    const T h = T(0.5);
+    T acc = T(0);
+    const T fo = s - l0;  // integrand at the anchor (the local origin)
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
+        if (fabs(A[k].z - s) <= tol) A[k].z = s;
+        if (fabs(B[k].z - s) <= tol) B[k].z = s;
         const T ca = A[k].z, cb = B[k].z;
-        const bool ia = ca < T(1), ib = cb < T(1);
+        const bool ia = KEEP_ABOVE ? (ca >= s) : (ca < s);
+        const bool ib = KEEP_ABOVE ? (cb >= s) : (cb < s);
+        P3<T> oa = A[k], ob = B[k];  // the part of the edge on the other side
+        bool off = !ia || !ib;
         if (ia != ib) {
-            const T t = fdiv(T(1) - ca, cb - ca);
-            const P3<T> I = mk<T>(fmaT(t, B[k].x - A[k].x, A[k].x), fmaT(t, B[k].y - A[k].y, A[k].y), T(1));
-            if (ia) {
-                hi2 += (I.x - h) * (B[k].y - h) - (I.y - h) * (B[k].x - h);
-                B[k] = I;
-                ex = I;
-            } else {
-                hi2 += (A[k].x - h) * (I.y - h) - (A[k].y - h) * (I.x - h);
-                A[k] = I;
-                en = I;
-            }
+            const T t = fdiv(s - ca, cb - ca);
+            const P3<T> I = mk<T>(fmaT(t, B[k].x - A[k].x, A[k].x), fmaT(t, B[k].y - A[k].y, A[k].y), s);
+            if (ia) { oa = I; B[k] = I; ex = I; } else { ob = I; A[k] = I; en = I; }
             got = true;
         } else if (!ia) {
-            hi2 += (A[k].x - h) * (B[k].y - h) - (A[k].y - h) * (B[k].x - h);
-            A[k] = o;
-            B[k] = o;
+            A[k] = z0;
+            B[k] = z0;
+        }
+        if (off) {
+            const T fa = s - fmaT(lx, oa.x, fmaT(ly, oa.y, l0));
+            const T fb = s - fmaT(lx, ob.x, fmaT(ly, ob.y, l0));
+            acc = fmaT(cross_xy(oa, ob), fo + fa + fb, acc);
         }
     }
     A[NE] = ex;
     B[NE] = en;
-    if (got) hi2 += (en.x - h) * (ex.y - h) - (en.y - h) * (ex.x - h);
-    return hi2;
+    if (got) {  // closing edge of the other part: entry -> exit
+        const T fa = s - fmaT(lx, en.x, fmaT(ly, en.y, l0));
+        const T fb = s - fmaT(lx, ex.x, fmaT(ly, ex.y, l0));
+        acc = fmaT(cross_xy(en, ex), fo + fa + fb, acc);
+    }
+    return acc;
 }
 
 // ---------------------------------------------------------------------------
-// Exact overlap volume of a positively oriented tetrahedron p[4] with [0,1]^3.
-// n[f], e[f]: outward face normals (unnormalised) and offsets in the cell frame
-// (inside iff n.x <= e); inv_n2[f] = 1/|n_f|^2.
+// Exact overlap volume of a positively oriented tetrahedron p[4] (cell frame:
+// the cell is [0,1)^3) with the cell.  n[f]: outward face normals (unnormalised,
+// face f opposite vertex f); (lx, ly): slopes of the plane l (0 for a horizontal
+// plane).  err receives the sum of the magnitudes of the terms.
 // ---------------------------------------------------------------------------
 template <class T>
-PSE_HD T overlap_volume(const P3<T> (&p)[4], const P3<T> (&n)[4], const T (&e)[4], const T (&inv_n2)[4])
+PSE_HD T overlap_volume(const P3<T> (&p)[4], const P3<T> (&n)[4], T lx, T ly, T &err)
 {
-    T vol = T(0);
+    // local frame
+    const T cx = T(0.25) * ((p[0].x + p[1].x) + (p[2].x + p[3].x));
+    const T cy = T(0.25) * ((p[0].y + p[1].y) + (p[2].y + p[3].y));
+    const T cz = T(0.25) * ((p[0].z + p[1].z) + (p[2].z + p[3].z));
+    const P3<T> q = mk<T>(floor(fmin(fmax(cx, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256),
+                          floor(fmin(fmax(cy, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256),
+                          floor(fmin(fmax(cz, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256));
+    P3<T> pl[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) pl[i] = sub(p[i], q);
+    const T xlo = -q.x, xhi = T(1) - q.x, ylo = -q.y, yhi = T(1) - q.y, zlo = -q.z, zhi = T(1) - q.z;
+    // reference plane l: slopes (lx, ly), through the centroid, but held inside the cell's
+    // z range at the column centre so that its values stay O(1) near the cell
+    const T xc = T(0.5) - q.x, yc = T(0.5) - q.y;
+    const T lc = fmin(fmax((cz - q.z) + lx * (xc - (cx - q.x)) + ly * (yc - (cy - q.y)), zlo), zhi);
+    const T l0 = lc - lx * xc - ly * yc;
+
+    T vol = T(0), mag = T(0);
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
         int ia, ib, ic;
         face_vertices(f, ia, ib, ic);
-        const P3<T> a = pick4(p, ia), b = pick4(p, ib), c = pick4(p, ic);
+        const P3<T> a = pick4(pl, ia), b = pick4(pl, ib), c = pick4(pl, ic);
         const T mnx = fmin(a.x, fmin(b.x, c.x)), mxx = fmax(a.x, fmax(b.x, c.x));
         const T mny = fmin(a.y, fmin(b.y, c.y)), mxy = fmax(a.y, fmax(b.y, c.y));
-        const T mnz = fmin(a.z, fmin(b.z, c.z)), mxz = fmax(a.z, fmax(b.z, c.z));
-        // outside the column, or entirely below z = 0 (clamp = 0): nothing
-        if (mxx < T(0) || mnx >= T(1) || mxy < T(0) || mny >= T(1) || mxz < T(0)) continue;
+        if (mxx < xlo || mnx >= xhi || mxy < ylo || mny >= yhi) continue;  // outside the column
         const P3<T> nf = (f == 0) ? n[0] : (f == 1) ? n[1] : (f == 2) ? n[2] : n[3];
-        if (nf.z == T(0)) continue;  // vertical face: zero projected area
-        const T ef = (f == 0) ? e[0] : (f == 1) ? e[1] : (f == 2) ? e[2] : e[3];
-        const T i2 = (f == 0) ? inv_n2[0] : (f == 1) ? inv_n2[1] : (f == 2) ? inv_n2[2] : inv_n2[3];
-        // anchor: the cell centre projected onto the face plane
-        const T sc = (T(0.5) * (nf.x + nf.y + nf.z) - ef) * i2;
-        const P3<T> o = mk<T>(T(0.5) - sc * nf.x, T(0.5) - sc * nf.y, T(0.5) - sc * nf.z);
+        if (nf.z == T(0)) continue;  // vertical face: no projected area
+        const T mnz = fmin(a.z, fmin(b.z, c.z)), mxz = fmax(a.z, fmax(b.z, c.z));
+        // snapping distance: a few units of rounding of this face's coordinates
+        const T cmag = fmax(T(1), fmax(fmax(fmax(fabs(mnx), fabs(mxx)), fmax(fabs(mny), fabs(mxy))),
+                                       fmax(fabs(mnz), fabs(mxz))));
+        const T tol = T(8) * std::numeric_limits<T>::epsilon() * cmag;
+        // anchor of the between-planes region: the local origin projected onto the face plane
+        const T n2 = dot(nf, nf);
+        const T sc = fdiv(dot(nf, a), n2);
+        const P3<T> o = mk<T>(sc * nf.x, sc * nf.y, sc * nf.z);
 
         P3<T> A[9], B[9];
         A[0] = a; B[0] = b;
         A[1] = b; B[1] = c;
         A[2] = c; B[2] = a;
-        bool cr;
-        if (mnx < T(0)) clip_plane<T, 0, false, 3>(A, B, o, cr); else collapse_slot<T, 3>(A, B, o);
-        if (mxx >= T(1)) clip_plane<T, 0, true, 4>(A, B, o, cr); else collapse_slot<T, 4>(A, B, o);
-        if (mny < T(0)) clip_plane<T, 1, false, 5>(A, B, o, cr); else collapse_slot<T, 5>(A, B, o);
-        if (mxy >= T(1)) clip_plane<T, 1, true, 6>(A, B, o, cr); else collapse_slot<T, 6>(A, B, o);
-        if (mnz < T(0)) clip_plane<T, 2, false, 7>(A, B, o, cr); else collapse_slot<T, 7>(A, B, o);
-        T hi2 = T(0);
-        if (mxz >= T(1)) hi2 = split_z1<T, 8>(A, B, o); else collapse_slot<T, 8>(A, B, o);
-        // below z = 1: projected integral of z, fan from the anchor
-        T acc = T(0);
+        if (mnx < xlo) clip_plane<T, 0, false, 3>(A, B, xlo, tol); else collapse_slot<T, 3>(A, B);
+        if (mxx >= xhi) clip_plane<T, 0, true, 4>(A, B, xhi, tol); else collapse_slot<T, 4>(A, B);
+        if (mny < ylo) clip_plane<T, 1, false, 5>(A, B, ylo, tol); else collapse_slot<T, 5>(A, B);
+        if (mxy >= yhi) clip_plane<T, 1, true, 6>(A, B, yhi, tol); else collapse_slot<T, 6>(A, B);
+        T below = T(0), above = T(0);
+        if (mnz < zlo) below = split_z<T, 7, true>(A, B, zlo, tol, l0, lx, ly); else collapse_slot<T, 7>(A, B);
+        if (mxz >= zhi) above = split_z<T, 8, false>(A, B, zhi, tol, l0, lx, ly); else collapse_slot<T, 8>(A, B);
+        // between the planes: integrand z - l, fan from o
+        const T fo = o.z - fmaT(lx, o.x, fmaT(ly, o.y, l0));
+        T mid = T(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-            const P3<T> u = sub(A[k], o), w = sub(B[k], o);
-            acc = fmaT(cross_xy(u, w), (o.z + A[k].z + B[k].z), acc);
+            const T fa = A[k].z - fmaT(lx, A[k].x, fmaT(ly, A[k].y, l0));
+            const T fb = B[k].z - fmaT(lx, B[k].x, fmaT(ly, B[k].y, l0));
+            mid = fmaT(cross_xy(sub(A[k], o), sub(B[k], o)), fo + fa + fb, mid);
         }
-        vol += acc * T(1.0 / 6.0) + T(0.5) * hi2;
+        vol += (below + above) + mid;
+        mag += fabs(below) + fabs(above) + fabs(mid);
     }
-    return vol;
+    err = mag * T(1.0 / 6.0);
+    return vol * T(1.0 / 6.0);
+}
+
+// Slopes of the reference plane l: the plane of the face whose normal is closest to
+// the z axis, unless that plane is steeper than 8 (then l is horizontal).
+template <class T>
+PSE_HD void ref_slopes(const P3<T> (&n)[4], T &lx, T &ly)
+{
+    int best = 0;
+    T bz = T(-1);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const T n2 = dot(n[f], n[f]);
+        const T r = (n2 > T(0)) ? n[f].z * n[f].z / n2 : T(0);
+        if (r > bz) { bz = r; best = f; }
+    }
+    const P3<T> nb = pick4(n, best);
+    lx = T(0);
+    ly = T(0);
+    if (nb.z != T(0)) {
+        lx = -nb.x / nb.z;
+        ly = -nb.y / nb.z;
+    }
+    if (!(fabs(lx) <= T(8) && fabs(ly) <= T(8))) {
+        lx = T(0);
+        ly = T(0);
+    }
+}
+
+// Outward face normals (face f opposite vertex f) of a positively oriented tetrahedron.
+template <class T>
+PSE_HD void face_normals(const P3<T> (&v)[4], P3<T> (&n)[4])
+{
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        int ia, ib, ic;
+        face_vertices(f, ia, ib, ic);
+        const P3<T> a = pick4(v, ia), b = pick4(v, ib), c = pick4(v, ic);
+        n[f] = cross(sub(b, a), sub(c, a));
+    }
+}
+
+// Overlap volume of a positively oriented tetrahedron (cell frame) computed in float64
+// from float32 vertices: the redo path of the FP32 guard.
+PSE_HD double overlap_volume_fp64(const P3<float> (&p)[4])
+{
+    P3<double> pd[4], nd[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pd[q] = mk<double>(p[q].x, p[q].y, p[q].z);
+    face_normals<double>(pd, nd);
+    double lx, ly, err;
+    ref_slopes<double>(nd, lx, ly);
+    return overlap_volume<double>(pd, nd, lx, ly, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -260,11 +372,11 @@ struct TetSetup {
     P3<T> v[4];     // vertices relative to the base cell corner, positively oriented
     P3<T> n[4];     // outward face normals (face f opposite vertex f)
     T e[4];         // n_f . x <= e_f inside (base-cell frame)
-    T inv_n2[4];
     T pos[4], neg[4];  // sum of positive / negative components of n_f (corner extremes)
     int lo[3], dim[3]; // bounding-box cells relative to the base: [lo, lo + dim)
     double vol6;       // |6 V| in grid units (float64)
     float kappa;       // conditioning estimate (surface * extent / volume)
+    T lx, ly;          // slopes of the reference plane l (the most horizontal face's plane)
 };
 
 template <class T>
@@ -297,7 +409,6 @@ PSE_HD void tet_setup(P3<T> (&v)[4], TetSetup<T> &s)
         const T n2 = dot(nn, nn);
         s.n[f] = nn;
         s.e[f] = dot(nn, a);
-        s.inv_n2[f] = (n2 > T(0)) ? T(1) / n2 : T(0);
         s.pos[f] = fmax(nn.x, T(0)) + fmax(nn.y, T(0)) + fmax(nn.z, T(0));
         s.neg[f] = fmin(nn.x, T(0)) + fmin(nn.y, T(0)) + fmin(nn.z, T(0));
         area2 += sqrt(n2);
@@ -329,6 +440,7 @@ PSE_HD void tet_setup(P3<T> (&v)[4], TetSetup<T> &s)
         s.lo[a] = lo[a];
         s.dim[a] = hi[a] - lo[a] + 1;
     }
+    ref_slopes<T>(s.n, s.lx, s.ly);
     const double denom = s.vol6 > 0.0 ? s.vol6 : 1e-300;
     s.kappa = (float)((double)area2 * sqrt((double)lmax2) / denom);
 }

@@ -63,7 +63,7 @@ struct DepositParams {
 
 // launchers (deposit.cu)
 cudaError_t launch_thread_per_tet(const DepositParams &p, bool fp64, bool stats, cudaStream_t st);
-cudaError_t launch_warp_coop(const DepositParams &p, bool stats, cudaStream_t st);
+cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_build_tets(const float *pos, const int64_t n[3], const int64_t nc[3], int periodic,
                               double box, int32_t *vidx, float *vol, int64_t n_tets, cudaStream_t st);
 

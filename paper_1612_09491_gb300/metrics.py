@@ -1,8 +1,11 @@
 """Cell-mass error measures used to state the accuracy of every result.
 
-max_rel: max_c |M[c] - R[c]| / max(R[c], floor * mean(R))   (floor = 1e-3)
+max_rel: max_c |M[c] - R[c]| / max(R[c], floor * Mbar)   (floor = 1e-3)
 l1:      sum_c |M[c] - R[c]| / sum_c R[c]
 mass:    |sum M - sum R| / sum R
+
+Mbar is the mean reference mass of the cells that hold mass (for a full lattice
+deposit every cell does, and Mbar is the plain mean cell mass).
 """
 from __future__ import annotations
 
@@ -14,7 +17,8 @@ def cell_errors(m, ref, floor: float = 1e-3) -> dict:
     r = np.asarray(ref, dtype=np.float64).ravel()
     d = np.abs(m - r)
     tot = r.sum()
-    mean = tot / max(r.size, 1)
+    occupied = int(np.count_nonzero(r))
+    mean = tot / max(occupied, 1)
     den = np.maximum(r, floor * mean) if mean > 0 else np.ones_like(r)
     return {
         "max_rel": float((d / den).max()) if d.size else 0.0,
