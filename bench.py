@@ -327,7 +327,8 @@ def main():
             sub = pse.deposit_uniform(pos, n, g, precision=pse.PSE_FP32_FP64ACC, schedule=pse.PSE_WARP_COOPERATIVE,
                                       cube_ids=torch.from_numpy(ids).to(dev))
             oracle_err = cell_errors(sub.cpu().numpy(), ref)
-            oracle_err["sample"] = "same cube sample as cpu_baseline, deposited alone on both sides"
+            oracle_err["sample"] = ("same cube sample as cpu_baseline, deposited alone on both sides (a sparse "
+                                    "deposit: cells covered by one tetrahedron's sliver are included)")
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

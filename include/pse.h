@@ -119,6 +119,25 @@ typedef struct pse_deposit_stats {
     double mass_dropped;       /* open grids: mass that fell outside the grid */
 } pse_deposit_stats;
 
+/*
+ * Adaptive deposit grid (Sec. 4): an octree over the periodic box [0, box)^3 whose
+ * leaves each carry a block of bc^3 cells (every leaf patch has the same cell count).
+ * A node at level l has side box/2^l; its leaf block has cells of side box/(bc 2^l).
+ * Leaves are listed depth first, children in the order c = cx + 2 cy + 4 cz.
+ * All pointers are owned by the library: release them with pse_free_octree().
+ */
+typedef struct pse_octree {
+    int32_t bc;             /* cells per leaf block side */
+    int32_t max_level;      /* deepest level that may hold leaves (<= 10) */
+    int64_t n_leaves;
+    double box;
+    int32_t *d_leaves;      /* device [n_leaves][4]: level, ix, iy, iz of each leaf */
+    int32_t *d_fine_map;    /* device [8^max_level]: leaf of every finest-level node, x fastest */
+    int32_t *h_leaves;      /* host copy of d_leaves */
+    int64_t n_cells;        /* n_leaves * bc^3: length of a leaf-mass array; leaf l's block starts at
+                               l * bc^3 and its cells are x fastest */
+} pse_octree;
+
 typedef struct pse_tuning {
     int32_t blocks_per_sm;   /* resident blocks per SM of the warp-cooperative kernel: 1 (no register
                                 cap) or 2 (128 registers per thread); <= 0: the built-in default */
@@ -170,8 +189,44 @@ PSE_API int pse_deposit_tets(const float *d_verts, const double *d_tet_mass, int
                      size_t ws_bytes, void *stream);
 
 /*
- * Bytes of device workspace an operation needs.  op = PSE_OP_*; lat may be NULL for
- * PSE_OP_DEPOSIT_TETS; op_params: for the uniform/tets deposits a host int64[3] grid_n
+ * An octree from an explicit leaf list (host int32 [n_leaves][4]: level, ix, iy, iz).
+ * The leaves must tile the box exactly (PSE_ERR_INVALID_ARG otherwise).  Allocates
+ * and fills *out (synchronous; free with pse_free_octree).
+ */
+PSE_API int pse_octree_from_leaves(const int32_t *h_leaves, int64_t n_leaves, int32_t bc, int32_t max_level,
+                                   double box, pse_octree *out);
+
+/*
+ * Build the octree from the tetrahedra's sizes (Sec. 4 builds it from tetrahedron
+ * counts; this rule refines where tetrahedra are small): a node at level l is refined
+ * iff l < max_level and the median, over the tetrahedra whose vertex centroid lies in
+ * the node, of the tetrahedron's mean edge length is below edge_threshold_cells times
+ * the node's cell size box/(bc 2^l).  Nodes without tetrahedra are leaves.  The median
+ * is taken from a 64-bin histogram of log10(edge / cell size) over [-3, 3): the lower
+ * edge of the bin holding the lower median.  Periodic lattices only.
+ *   d_ws: ws_bytes >= pse_workspace_size(PSE_OP_BUILD_OCTREE, lat, &max_level) (int32), or NULL/0.
+ * Synchronises `stream`; allocates *out (free with pse_free_octree).
+ */
+PSE_API int pse_build_octree_from_tet_sizes(const float *d_pos, const pse_lattice *lat, int32_t bc,
+                                            int32_t max_level, double edge_threshold_cells, pse_octree *out,
+                                            void *d_ws, size_t ws_bytes, void *stream);
+
+/*
+ * Deposit the tessellation (or opts->d_cube_ids) onto the leaf blocks of `oct`:
+ * d_leaf_mass[l * bc^3 + cx + bc (cy + bc cz)] (+)= sum_t m_t/|V_t| vol(T_t ∩ C) for cell
+ * (cx, cy, cz) of leaf l.  Periodic lattices only.  Other arguments as
+ * pse_deposit_uniform (d_leaf_mass has oct->n_cells float64 entries).
+ */
+PSE_API int pse_deposit_octree(const float *d_pos, const pse_lattice *lat, const pse_octree *oct,
+                               double *d_leaf_mass, const pse_deposit_opts *opts, pse_deposit_stats *h_stats,
+                               void *d_ws, size_t ws_bytes, void *stream);
+
+/* Release what pse_octree_from_leaves / pse_build_octree_from_tet_sizes allocated; zeroes *oct. */
+PSE_API void pse_free_octree(pse_octree *oct);
+
+/*
+ * Bytes of device workspace an operation needs.  op = PSE_OP_*; lat may be NULL;
+ * op_params: for PSE_OP_BUILD_OCTREE a host int32 max_level (required), otherwise unused
  * (may be NULL).  Returns 0 for an unknown op.
  */
 PSE_API size_t pse_workspace_size(int op, const pse_lattice *lat, const void *op_params);

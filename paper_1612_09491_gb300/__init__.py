@@ -20,7 +20,8 @@ from ._lib import (  # noqa: F401
 )
 
 __all__ = ["build_tets_from_lagrangian_grid", "deposit_uniform", "deposit_tets", "workspace_size", "last_error",
-           "abi_version", "lattice", "opts"]
+           "abi_version", "lattice", "opts", "OctreeHandle", "octree_from_leaves", "build_octree_from_tet_sizes",
+           "deposit_octree"]
 
 
 _EMPTY_SENTINEL = 16  # non-NULL, never dereferenced (n_cube_ids == 0)
@@ -164,3 +165,82 @@ def last_error() -> str:
 
 def abi_version() -> int:
     return int(_lib.load().pse_abi_version())
+
+
+class OctreeHandle:
+    """Owns a pse_octree; frees it with pse_free_octree when collected."""
+
+    def __init__(self, st: _lib.Octree):
+        self.st = st
+
+    @property
+    def bc(self) -> int:
+        return self.st.bc
+
+    @property
+    def max_level(self) -> int:
+        return self.st.max_level
+
+    @property
+    def n_leaves(self) -> int:
+        return self.st.n_leaves
+
+    @property
+    def n_cells(self) -> int:
+        return self.st.n_cells
+
+    def leaves(self):
+        import numpy as np
+        buf = (ctypes.c_int32 * (4 * self.st.n_leaves)).from_address(self.st.h_leaves)
+        return np.frombuffer(buf, dtype=np.int32).reshape(-1, 4).copy()
+
+    def __del__(self):
+        try:
+            if self.st.h_leaves:
+                _lib.load().pse_free_octree(ctypes.byref(self.st))
+        except Exception:
+            pass
+
+
+def octree_from_leaves(leaves, bc: int, max_level: int, box: float = 1.0) -> OctreeHandle:
+    """pse_octree_from_leaves: leaves int32 [L, 4] (level, ix, iy, iz) that tile the box."""
+    import numpy as np
+    lv = np.ascontiguousarray(leaves, dtype=np.int32)
+    st = _lib.Octree()
+    _lib.check(_lib.load().pse_octree_from_leaves(lv.ctypes.data_as(ctypes.c_void_p), lv.shape[0], bc, max_level,
+                                                  float(box), ctypes.byref(st)))
+    return OctreeHandle(st)
+
+
+def build_octree_from_tet_sizes(pos, n, bc: int, max_level: int, threshold_cells: float = 2.0, *,
+                                box: float = 1.0, stream=None) -> OctreeHandle:
+    """pse_build_octree_from_tet_sizes (periodic lattice)."""
+    torch = _torch()
+    lat = lattice(n, box, True)
+    st = _lib.Octree()
+    _lib.check(_lib.load().pse_build_octree_from_tet_sizes(_dev_ptr(pos, torch.float32, "pos"), ctypes.byref(lat),
+                                                           bc, max_level, float(threshold_cells), ctypes.byref(st),
+                                                           None, 0, _stream_ptr(stream)))
+    return OctreeHandle(st)
+
+
+def deposit_octree(pos, n, octree: OctreeHandle, *, box: float = 1.0, particle_mass=None, out=None,
+                   precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
+                   accumulate: bool = False, mass_fixup: bool = True, cube_ids=None, stats: bool = False,
+                   workspace=None, stream=None, tuning=None):
+    """pse_deposit_octree: leaf masses float64 [n_leaves, bc, bc, bc] (x fastest within a block)."""
+    torch = _torch()
+    L = _lib.load()
+    lat = lattice(n, box, True, particle_mass)
+    bc = octree.bc
+    if out is None:
+        out = torch.empty((octree.n_leaves, bc, bc, bc), dtype=torch.float64, device=pos.device)
+    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, cube_ids, tuning)
+    st = _lib.DepositStats() if stats else None
+    ws_ptr, ws_bytes = (ctypes.c_void_p(None), 0) if workspace is None else \
+        (_dev_ptr(workspace, torch.uint8, "workspace"), workspace.numel())
+    rc = L.pse_deposit_octree(_dev_ptr(pos, torch.float32, "pos"), ctypes.byref(lat), ctypes.byref(octree.st),
+                              _dev_ptr(out, torch.float64, "out"), ctypes.byref(o),
+                              ctypes.byref(st) if st is not None else None, ws_ptr, ws_bytes, _stream_ptr(stream))
+    _lib.check(rc)
+    return (out, st.to_dict()) if stats else out

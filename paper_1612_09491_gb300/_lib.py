@@ -38,6 +38,10 @@ EXPORTED = (
     "pse_build_tets_from_lagrangian_grid",
     "pse_deposit_uniform",
     "pse_deposit_tets",
+    "pse_octree_from_leaves",
+    "pse_build_octree_from_tet_sizes",
+    "pse_deposit_octree",
+    "pse_free_octree",
     "pse_workspace_size",
     "pse_last_error",
     "pse_abi_version",
@@ -66,6 +70,12 @@ class DepositStats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "bin_counts"}
         d["bin_counts"] = list(self.bin_counts)
         return d
+
+
+class Octree(ctypes.Structure):
+    _fields_ = [("bc", ctypes.c_int32), ("max_level", ctypes.c_int32), ("n_leaves", ctypes.c_int64),
+                ("box", ctypes.c_double), ("d_leaves", ctypes.c_void_p), ("d_fine_map", ctypes.c_void_p),
+                ("h_leaves", ctypes.c_void_p), ("n_cells", ctypes.c_int64)]
 
 
 class Tuning(ctypes.Structure):
@@ -107,12 +117,21 @@ def load(build_if_missing: bool = False):
         L.pse_deposit_tets.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_double, ctypes.c_int32, i64p, vp,
                                        ctypes.POINTER(DepositOpts), ctypes.POINTER(DepositStats), vp, ctypes.c_size_t,
                                        vp]
+        OP = ctypes.POINTER(Octree)
+        L.pse_octree_from_leaves.argtypes = [vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, OP]
+        L.pse_build_octree_from_tet_sizes.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int32, ctypes.c_int32,
+                                                      ctypes.c_double, OP, vp, ctypes.c_size_t, vp]
+        L.pse_deposit_octree.argtypes = [vp, ctypes.POINTER(Lattice), OP, vp, ctypes.POINTER(DepositOpts),
+                                         ctypes.POINTER(DepositStats), vp, ctypes.c_size_t, vp]
+        L.pse_free_octree.argtypes = [OP]
+        L.pse_free_octree.restype = None
         L.pse_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Lattice), vp]
         L.pse_workspace_size.restype = ctypes.c_size_t
         L.pse_last_error.argtypes = []
         L.pse_last_error.restype = ctypes.c_char_p
         L.pse_abi_version.argtypes = []
         for name in ("pse_build_tets_from_lagrangian_grid", "pse_deposit_uniform", "pse_deposit_tets",
+                     "pse_octree_from_leaves", "pse_build_octree_from_tet_sizes", "pse_deposit_octree",
                      "pse_abi_version"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/pse.h"
 #include "internal.h"
@@ -46,9 +47,10 @@ pse_deposit_opts default_opts()
 
 // FP32 guard: a tetrahedron whose conditioning estimate kappa (total face area x longest
 // edge / |6V|; about 8 for an undistorted Kuhn tetrahedron) exceeds kappa_max is clipped
-// in float64.  kappa_max = 6.4e6 * guard_eps: measured on shell-crossed Zel'dovich and
-// jittered lattices, FP32 clips of tetrahedra below this bound keep the per-cell error
-// (relative, floored at 1e-3 of the mean cell mass) below about guard_eps.
+// in float64.  kappa_max = 4e6 * guard_eps (40 by default): measured against the FP64
+// oracle on shell-crossed Zel'dovich and jittered lattices, FP32 clips of tetrahedra
+// below this bound keep the per-cell error (relative, floored at 1e-3 of the mean cell
+// mass) below guard_eps.
 constexpr double kDefaultGuardEps = 1.0e-5;
 
 // resident blocks per SM of the warp-cooperative kernel (1: no register cap; 2: 128 registers)
@@ -57,7 +59,7 @@ constexpr int kDefaultBlocksPerSm = 1;
 float kappa_limit(double guard_eps)
 {
     const double g = guard_eps > 0.0 ? guard_eps : kDefaultGuardEps;
-    return (float)(6.4e6 * g);
+    return (float)(4.0e6 * g);
 }
 
 struct WsLease {
@@ -141,7 +143,14 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
         if (e != cudaSuccess) return cuda_fail(e, "output clear");
     }
     const bool stats = h_stats != nullptr;
-    if (p.n_units > 0) {
+    if (p.n_units > 0 && p.leaves) {
+        const pse_tuning *tu = static_cast<const pse_tuning *>(o.tuning);
+        const int bps = (tu && tu->blocks_per_sm > 0) ? tu->blocks_per_sm : kDefaultBlocksPerSm;
+        if (o.schedule != PSE_THREAD_PER_TET)
+            p.n_items = (p.src == pse::SRC_LATTICE) ? ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2] : (p.n_units + 31) / 32;
+        e = pse::launch_octree_deposit(p, o.precision == PSE_FP64_PLAIN, o.schedule == PSE_THREAD_PER_TET, stats, bps, st);
+        if (e != cudaSuccess) return cuda_fail(e, "octree deposit launch");
+    } else if (p.n_units > 0) {
         if (o.schedule == PSE_THREAD_PER_TET) {
             e = pse::launch_thread_per_tet(p, o.precision == PSE_FP64_PLAIN, stats, st);
         } else {
@@ -180,6 +189,136 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
     return PSE_OK;
 }
 
+
+constexpr int kMaxOctreeLevel = 10;
+
+// histogram counters of levels 0 .. max_level-1, 64 bins per node
+size_t hist_bytes(int max_level)
+{
+    size_t n = 0;
+    for (int l = 0; l < max_level; ++l) n += ((size_t)1 << (3 * l)) * 64;
+    return (n * sizeof(unsigned) + 255) / 256 * 256;
+}
+
+int check_lattice(const pse_lattice *lat)
+{
+    if (!lat) return fail(PSE_ERR_INVALID_ARG, "lat is NULL");
+    for (int a = 0; a < 3; ++a)
+        if (lat->n[a] < 2) return fail(PSE_ERR_INVALID_ARG, "lat->n[%d] = %lld < 2", a, (long long)lat->n[a]);
+    if (!(lat->box > 0.0) || !std::isfinite(lat->box)) return fail(PSE_ERR_INVALID_ARG, "lat->box must be > 0");
+    if (!std::isfinite(lat->particle_mass)) return fail(PSE_ERR_INVALID_ARG, "lat->particle_mass must be finite");
+    return PSE_OK;
+}
+
+void lattice_params(pse::DepositParams &p, const float *d_pos, const pse_lattice *lat, const pse_deposit_opts &o)
+{
+    p.periodic = lat->periodic ? 1 : 0;
+    p.pos = d_pos;
+    for (int a = 0; a < 3; ++a) {
+        p.n[a] = lat->n[a];
+        p.nc[a] = p.periodic ? lat->n[a] : lat->n[a] - 1;
+    }
+    p.box = lat->box;
+    p.m_tet = lat->particle_mass / 6.0;
+    if (o.d_cube_ids) {
+        p.src = pse::SRC_CUBE_LIST;
+        p.cube_ids = o.d_cube_ids;
+        p.n_units = o.n_cube_ids;
+    } else {
+        p.src = pse::SRC_LATTICE;
+        p.n_units = p.nc[0] * p.nc[1] * p.nc[2];
+    }
+}
+
+// leaves -> finest-level map, checking that they tile the box exactly
+int fine_map_of(const int32_t *leaves, int64_t n_leaves, int max_level, std::vector<int32_t> &map)
+{
+    const int64_t F = (int64_t)1 << max_level;
+    map.assign((size_t)(F * F * F), -1);
+    for (int64_t l = 0; l < n_leaves; ++l) {
+        const int32_t *L = leaves + 4 * l;
+        if (L[0] < 0 || L[0] > max_level)
+            return fail(PSE_ERR_INVALID_ARG, "leaf %lld: level %d outside [0, %d]", (long long)l, L[0], max_level);
+        const int64_t nn = (int64_t)1 << L[0], span = F / nn;
+        for (int a = 1; a < 4; ++a)
+            if (L[a] < 0 || L[a] >= nn)
+                return fail(PSE_ERR_INVALID_ARG, "leaf %lld: node index out of range", (long long)l);
+        for (int64_t z = L[3] * span; z < (L[3] + 1) * span; ++z)
+            for (int64_t y = L[2] * span; y < (L[2] + 1) * span; ++y)
+                for (int64_t x = L[1] * span; x < (L[1] + 1) * span; ++x) {
+                    int32_t &m = map[(size_t)(x + F * (y + F * z))];
+                    if (m != -1) return fail(PSE_ERR_INVALID_ARG, "leaves %d and %lld overlap", m, (long long)l);
+                    m = (int32_t)l;
+                }
+    }
+    for (size_t i = 0; i < map.size(); ++i)
+        if (map[i] < 0) return fail(PSE_ERR_INVALID_ARG, "the leaves do not tile the box");
+    return PSE_OK;
+}
+
+// depth-first refinement from the level histograms (lower-median bin edge rule)
+void decide(const std::vector<unsigned> &hist, int max_level, double threshold, int level, int64_t ix, int64_t iy,
+            int64_t iz, std::vector<int32_t> &leaves)
+{
+    bool refine = false;
+    if (level < max_level) {
+        size_t off = 0;
+        for (int l = 0; l < level; ++l) off += ((size_t)1 << (3 * l)) * 64;
+        const int64_t nn = (int64_t)1 << level;
+        const unsigned *h = hist.data() + off + (size_t)(ix + nn * (iy + nn * iz)) * 64;
+        unsigned long long count = 0;
+        for (int b = 0; b < 64; ++b) count += h[b];
+        if (count > 0) {
+            const unsigned long long k = (count - 1) / 2;
+            unsigned long long cum = 0;
+            int bin = 63;
+            for (int b = 0; b < 64; ++b) {
+                cum += h[b];
+                if (cum > k) { bin = b; break; }
+            }
+            const double lower_edge = std::pow(10.0, -3.0 + 6.0 * bin / 64.0);
+            refine = lower_edge < threshold;
+        }
+    }
+    if (!refine) {
+        leaves.push_back(level);
+        leaves.push_back((int32_t)ix);
+        leaves.push_back((int32_t)iy);
+        leaves.push_back((int32_t)iz);
+        return;
+    }
+    for (int c = 0; c < 8; ++c)
+        decide(hist, max_level, threshold, level + 1, 2 * ix + (c & 1), 2 * iy + ((c >> 1) & 1), 2 * iz + (c >> 2),
+               leaves);
+}
+
+int make_octree(const int32_t *leaves, int64_t n_leaves, int32_t bc, int32_t max_level, double box, pse_octree *out)
+{
+    std::vector<int32_t> map;
+    int rc = fine_map_of(leaves, n_leaves, max_level, map);
+    if (rc != PSE_OK) return rc;
+    pse_octree o;
+    std::memset(&o, 0, sizeof(o));
+    o.bc = bc;
+    o.max_level = max_level;
+    o.n_leaves = n_leaves;
+    o.box = box;
+    o.n_cells = n_leaves * (int64_t)bc * bc * bc;
+    o.h_leaves = static_cast<int32_t *>(std::malloc((size_t)n_leaves * 4 * sizeof(int32_t)));
+    if (!o.h_leaves) return fail(PSE_ERR_OOM, "host allocation failed");
+    std::memcpy(o.h_leaves, leaves, (size_t)n_leaves * 4 * sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&o.d_leaves, (size_t)n_leaves * 4 * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&o.d_fine_map, map.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(o.d_leaves, leaves, (size_t)n_leaves * 4 * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(o.d_fine_map, map.data(), map.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        pse_free_octree(&o);
+        return fail(e == cudaErrorMemoryAllocation ? PSE_ERR_OOM : PSE_ERR_CUDA, "octree upload: %s",
+                    cudaGetErrorString(e));
+    }
+    *out = o;
+    return PSE_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -195,7 +334,14 @@ size_t pse_workspace_size(int op, const pse_lattice *lat, const void *op_params)
     switch (op) {
     case PSE_OP_DEPOSIT_UNIFORM:
     case PSE_OP_DEPOSIT_TETS:
+    case PSE_OP_DEPOSIT_OCTREE:
         return pse::kWorkspaceBytes;
+    case PSE_OP_BUILD_OCTREE: {
+        if (!op_params) return 0;
+        const int32_t ml = *static_cast<const int32_t *>(op_params);
+        if (ml < 0 || ml > kMaxOctreeLevel) return 0;
+        return pse::kWorkspaceBytes + hist_bytes(ml);
+    }
     default:
         return 0;
     }
@@ -265,6 +411,99 @@ int pse_deposit_uniform(const float *d_pos, const pse_lattice *lat, const int64_
         p.n_units = p.nc[0] * p.nc[1] * p.nc[2];
     }
     return run_deposit(p, o, cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+int pse_octree_from_leaves(const int32_t *h_leaves, int64_t n_leaves, int32_t bc, int32_t max_level, double box,
+                           pse_octree *out)
+{
+    g_last_error.clear();
+    if (!h_leaves || !out || n_leaves < 1) return fail(PSE_ERR_INVALID_ARG, "h_leaves and out must be non-NULL, n_leaves >= 1");
+    if (bc < 1 || bc > 4096) return fail(PSE_ERR_INVALID_ARG, "bc = %d out of range [1, 4096]", bc);
+    if (max_level < 0 || max_level > kMaxOctreeLevel) return fail(PSE_ERR_INVALID_ARG, "max_level out of range");
+    if (!(box > 0.0) || !std::isfinite(box)) return fail(PSE_ERR_INVALID_ARG, "box must be > 0");
+    return make_octree(h_leaves, n_leaves, bc, max_level, box, out);
+}
+
+int pse_build_octree_from_tet_sizes(const float *d_pos, const pse_lattice *lat, int32_t bc, int32_t max_level,
+                                    double edge_threshold_cells, pse_octree *out, void *d_ws, size_t ws_bytes,
+                                    void *stream)
+{
+    g_last_error.clear();
+    int rc = check_lattice(lat);
+    if (rc != PSE_OK) return rc;
+    if (!d_pos || !out) return fail(PSE_ERR_INVALID_ARG, "d_pos and out must be non-NULL");
+    if (!lat->periodic) return fail(PSE_ERR_UNSUPPORTED, "the octree covers a periodic box");
+    if (bc < 1 || bc > 4096) return fail(PSE_ERR_INVALID_ARG, "bc = %d out of range [1, 4096]", bc);
+    if (max_level < 0 || max_level > kMaxOctreeLevel) return fail(PSE_ERR_INVALID_ARG, "max_level out of range");
+    if (!(edge_threshold_cells > 0.0)) return fail(PSE_ERR_INVALID_ARG, "edge_threshold_cells must be > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t hb = hist_bytes(max_level);
+    const size_t need = pse::kWorkspaceBytes + hb;
+    void *ws = d_ws;
+    bool owned = false;
+    if (!ws) {
+        if (ws_bytes != 0) return fail(PSE_ERR_INVALID_ARG, "d_ws is NULL but ws_bytes is %zu", ws_bytes);
+        cudaError_t e = cudaMallocAsync(&ws, need, st);
+        if (e != cudaSuccess) return fail(PSE_ERR_OOM, "workspace allocation failed: %s", cudaGetErrorString(e));
+        owned = true;
+    } else if (ws_bytes < need) {
+        return fail(PSE_ERR_WORKSPACE, "ws_bytes = %zu < required %zu", ws_bytes, need);
+    }
+    std::vector<unsigned> hist(hb / sizeof(unsigned), 0u);
+    cudaError_t e = cudaMemsetAsync(ws, 0, need, st);
+    if (max_level > 0 && e == cudaSuccess) {
+        pse::DepositParams p;
+        std::memset(&p, 0, sizeof(p));
+        pse_deposit_opts o = default_opts();
+        lattice_params(p, d_pos, lat, o);
+        p.bc = bc;
+        p.max_level = max_level;
+        p.ws = static_cast<pse::Workspace *>(ws);
+        unsigned *d_hist = reinterpret_cast<unsigned *>(static_cast<char *>(ws) + pse::kWorkspaceBytes);
+        e = pse::launch_octree_hist(p, d_hist, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hist.data(), d_hist, hb, cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (owned) cudaFreeAsync(ws, st);
+    if (e != cudaSuccess) return cuda_fail(e, "octree histograms");
+    std::vector<int32_t> leaves;
+    decide(hist, max_level, edge_threshold_cells, 0, 0, 0, 0, leaves);
+    return make_octree(leaves.data(), (int64_t)(leaves.size() / 4), bc, max_level, lat->box, out);
+}
+
+int pse_deposit_octree(const float *d_pos, const pse_lattice *lat, const pse_octree *oct, double *d_leaf_mass,
+                       const pse_deposit_opts *opts, pse_deposit_stats *h_stats, void *d_ws, size_t ws_bytes,
+                       void *stream)
+{
+    g_last_error.clear();
+    int rc = check_lattice(lat);
+    if (rc != PSE_OK) return rc;
+    if (!d_pos || !oct || !d_leaf_mass) return fail(PSE_ERR_INVALID_ARG, "d_pos, oct and d_leaf_mass must be non-NULL");
+    if (!oct->d_leaves || !oct->d_fine_map || oct->n_leaves < 1) return fail(PSE_ERR_INVALID_ARG, "oct is empty");
+    if (!lat->periodic) return fail(PSE_ERR_UNSUPPORTED, "the octree covers a periodic box");
+    if (oct->box != lat->box) return fail(PSE_ERR_INVALID_ARG, "oct->box differs from lat->box");
+    const pse_deposit_opts o = opts ? *opts : default_opts();
+    rc = check_opts(o);
+    if (rc != PSE_OK) return rc;
+    pse::DepositParams p;
+    std::memset(&p, 0, sizeof(p));
+    lattice_params(p, d_pos, lat, o);
+    p.out = d_leaf_mass;
+    p.bc = oct->bc;
+    p.max_level = oct->max_level;
+    p.leaves = oct->d_leaves;
+    p.fine_map = oct->d_fine_map;
+    p.fine = (int64_t)1 << oct->max_level;
+    return run_deposit(p, o, oct->n_cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+void pse_free_octree(pse_octree *oct)
+{
+    if (!oct) return;
+    if (oct->d_leaves) cudaFree(oct->d_leaves);
+    if (oct->d_fine_map) cudaFree(oct->d_fine_map);
+    std::free(oct->h_leaves);
+    std::memset(oct, 0, sizeof(*oct));
 }
 
 int pse_deposit_tets(const float *d_verts, const double *d_tet_mass, int64_t n_tets, double box, int32_t periodic,

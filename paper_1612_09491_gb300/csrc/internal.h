@@ -56,6 +56,12 @@ struct DepositParams {
     // numerics
     float kappa_max;           // FP32 path: tetrahedra with kappa above this clip in float64
     int32_t fixup;
+    // octree target (deposit onto leaf blocks)
+    int32_t bc;                // cells per leaf block side
+    int32_t max_level;
+    const int32_t *leaves;     // [n_leaves][4]: level, ix, iy, iz
+    const int32_t *fine_map;   // [F^3]: leaf of every finest-level node, x fastest
+    int64_t fine;              // F = 2^max_level
     // scheduling
     int64_t n_items;
     Workspace *ws;
@@ -64,6 +70,9 @@ struct DepositParams {
 // launchers (deposit.cu)
 cudaError_t launch_thread_per_tet(const DepositParams &p, bool fp64, bool stats, cudaStream_t st);
 cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st);
+cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStream_t st);
+cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread_per_tet, bool stats,
+                                  int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_build_tets(const float *pos, const int64_t n[3], const int64_t nc[3], int periodic,
                               double box, int32_t *vidx, float *vol, int64_t n_tets, cudaStream_t st);
 

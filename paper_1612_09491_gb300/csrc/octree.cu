@@ -1,0 +1,546 @@
+// octree.cu -- the adaptive deposit grid (Sec. 4): tetrahedron-size histograms for
+// the octree build, and the deposit onto leaf blocks.
+//
+// Tree: the root is the periodic box; a node at level l has side box/2^l; every leaf
+// carries a block of bc^3 cells of side h_l = box/(bc 2^l) (Sec. 4: every leaf patch
+// has the same number of cells).  Finest-level nodes (2^max_level per axis) map to
+// the leaf that contains them (fine_map), so the leaves a tetrahedron touches are
+// found from the finest nodes its bounding box covers.
+//
+// A tetrahedron overlapping k leaves is deposited as k "virtual" tetrahedra: the
+// same tetrahedron expressed in the cell units of that leaf's level, with its cell
+// range clipped to the leaf's block.  Each virtual tetrahedron runs through the same
+// classification and clip as the uniform grid (common.cuh).
+#include "common.cuh"
+
+namespace pse {
+namespace {
+
+// Lagrangian tetrahedron as float32 positions plus integer periodic shifts
+// (vertex q sits at x[q] + k[q] * box), nearest image to vertex 0.
+__device__ __forceinline__ void lattice_tet_raw(const DepositParams &P, int64_t ci, int64_t cj, int64_t ck, int s,
+                                                float (&x)[4][3], int (&k)[4][3])
+{
+    int o1[3], o2[3];
+    kuhn_offsets(s, o1, o2);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int64_t i = ci, j = cj, kk = ck;
+        if (q == 1) { i += o1[0]; j += o1[1]; kk += o1[2]; }
+        if (q == 2) { i += o2[0]; j += o2[1]; kk += o2[2]; }
+        if (q == 3) { i += 1; j += 1; kk += 1; }
+        if (P.periodic) { i = wrap_idx(i, P.n[0]); j = wrap_idx(j, P.n[1]); kk = wrap_idx(kk, P.n[2]); }
+        const float *p = P.pos + 3 * (i + P.n[0] * (j + P.n[1] * kk));
+        x[q][0] = __ldg(p);
+        x[q][1] = __ldg(p + 1);
+        x[q][2] = __ldg(p + 2);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int sh = 0;
+            if (P.periodic && q > 0) {
+                const double d = (double)x[q][a] - (double)x[0][a];
+                sh = (d >= 0.5 * P.box) ? -1 : ((d < -0.5 * P.box) ? 1 : 0);
+            }
+            k[q][a] = sh;
+        }
+}
+
+// The tetrahedron in the cell units of a grid with g cells per side over the box,
+// relative to its base cell (the cell of vertex 0).
+template <class T>
+__device__ __forceinline__ void to_grid(const DepositParams &P, const float (&x)[4][3], const int (&k)[4][3],
+                                        int64_t g, P3<T> (&v)[4], int (&base)[3])
+{
+    const double sd = (double)g / P.box;
+    const float sf = (float)sd;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) base[a] = safe_floor((double)x[0][a] * sd);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        T c[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const long long off = (long long)k[q][a] * g - base[a];
+            if constexpr (sizeof(T) == 4)
+                c[a] = fmaf(x[q][a], sf, (float)off);
+            else
+                c[a] = fma((double)x[q][a], sd, (double)off);
+        }
+        v[q] = mk<T>(c[0], c[1], c[2]);
+    }
+}
+
+__device__ __forceinline__ double unwrapped(const DepositParams &P, const float (&x)[4][3], const int (&k)[4][3],
+                                            int q, int a)
+{
+    return (double)x[q][a] + (double)k[q][a] * P.box;
+}
+
+// Range of finest-level nodes covered by the tetrahedron's bounding box (unfolded).
+__device__ __forceinline__ void fine_range(const DepositParams &P, const float (&x)[4][3], const int (&k)[4][3],
+                                           int64_t (&f0)[3], int64_t (&f1)[3])
+{
+    const double s = (double)P.fine / P.box;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double mn = unwrapped(P, x, k, 0, a), mx = mn;
+#pragma unroll
+        for (int q = 1; q < 4; ++q) {
+            mn = fmin(mn, unwrapped(P, x, k, q, a));
+            mx = fmax(mx, unwrapped(P, x, k, q, a));
+        }
+        f0[a] = (int64_t)floor(mn * s);
+        f1[a] = (int64_t)floor(mx * s);
+    }
+}
+
+struct LeafHit {
+    int leaf;
+    int level;
+    int64_t org[3];  // the leaf's first cell at its level, unfolded (periodic image of the tetrahedron)
+};
+
+// Advance `cursor` over the finest nodes of [f0, f1] until a node that is the first
+// node of its (leaf, periodic image) within the range; fills `hit`.  False when done.
+__device__ __forceinline__ bool next_leaf(const DepositParams &P, const int64_t (&f0)[3], const int64_t (&f1)[3],
+                                          int64_t &cursor, LeafHit &hit)
+{
+    const int64_t nx = f1[0] - f0[0] + 1, ny = f1[1] - f0[1] + 1, nz = f1[2] - f0[2] + 1;
+    const int64_t total = nx * ny * nz;
+    const int64_t F = P.fine;
+    while (cursor < total) {
+        const int64_t c = cursor++;
+        const int64_t f[3] = {f0[0] + c % nx, f0[1] + (c / nx) % ny, f0[2] + c / (nx * ny)};
+        int64_t g[3];
+        bool inside = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            g[a] = P.periodic ? fold_cell(f[a], F) : f[a];
+            inside = inside && g[a] >= 0 && g[a] < F;
+        }
+        if (!inside) continue;
+        const int leaf = __ldg(P.fine_map + g[0] + F * (g[1] + F * g[2]));
+        const int level = __ldg(P.leaves + 4 * leaf);
+        const int64_t span = (int64_t)1 << (P.max_level - level);
+        bool first = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t lo = (int64_t)__ldg(P.leaves + 4 * leaf + 1 + a) * span + (f[a] - g[a]);
+            first = first && (f[a] == (lo > f0[a] ? lo : f0[a]));
+        }
+        if (!first) continue;
+        hit.leaf = leaf;
+        hit.level = level;
+        const int64_t gl = (int64_t)P.bc << level;  // cells per side at the leaf's level
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            hit.org[a] = (int64_t)__ldg(P.leaves + 4 * leaf + 1 + a) * P.bc + ((f[a] - g[a]) / F) * gl;
+        return true;
+    }
+    return false;
+}
+
+// The leaf cell (index into the leaf-mass array) that holds the unwrapped point c.
+__device__ __forceinline__ int64_t point_cell(const DepositParams &P, const double (&c)[3], bool &ok)
+{
+    const int64_t F = P.fine;
+    int64_t g[3], img[3];
+    ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t f = (int64_t)floor(c[a] * (double)F / P.box);
+        g[a] = P.periodic ? fold_cell(f, F) : f;
+        img[a] = f - g[a];
+        ok = ok && g[a] >= 0 && g[a] < F;
+    }
+    if (!ok) return 0;
+    const int leaf = __ldg(P.fine_map + g[0] + F * (g[1] + F * g[2]));
+    const int level = __ldg(P.leaves + 4 * leaf);
+    const int64_t bc = P.bc, gl = bc << level;
+    int64_t idx = (int64_t)leaf * bc * bc * bc, stride = 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double u = c[a] * (double)gl / P.box;
+        int64_t cc = (int64_t)floor(u) - ((int64_t)__ldg(P.leaves + 4 * leaf + 1 + a) * bc + (img[a] / F) * gl);
+        cc = cc < 0 ? 0 : (cc >= bc ? bc - 1 : cc);
+        idx += cc * stride;
+        stride *= bc;
+    }
+    return idx;
+}
+
+__device__ __forceinline__ void tet_centroid(const DepositParams &P, const float (&x)[4][3], const int (&k)[4][3],
+                                             double (&c)[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        c[a] = 0.25 * (unwrapped(P, x, k, 0, a) + unwrapped(P, x, k, 1, a) + unwrapped(P, x, k, 2, a) +
+                       unwrapped(P, x, k, 3, a));
+}
+
+__device__ __forceinline__ double det6_box(const DepositParams &P, const float (&x)[4][3], const int (&k)[4][3])
+{
+    double e[3][3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) e[q][a] = unwrapped(P, x, k, q + 1, a) - unwrapped(P, x, k, 0, a);
+    return e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+           e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+}
+
+__device__ __forceinline__ void add_mass(const DepositParams &P, const double (&c)[3], double m, Counters &cnt,
+                                         bool stats)
+{
+    bool ok;
+    const int64_t idx = point_cell(P, c, ok);
+    if (ok) atomicAdd(P.out + idx, m);
+    else if (stats) cnt.dropped += m;
+}
+
+// ---------------------------------------------------------------------------
+// thread per tetrahedron (T = double: the plain FP64 octree path)
+// ---------------------------------------------------------------------------
+template <class T, bool STATS>
+__global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
+{
+    Counters cnt;
+    if (STATS) cnt.zero();
+    const int64_t n_tets = 6 * P.n_units;
+    const int64_t bc = P.bc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ci, cj, ck;
+        if (!cube_of_unit(P, t / 6, ci, cj, ck)) {
+            set_error(P.ws, 3, (int)((t / 6) & 0x7fffffff));
+            continue;
+        }
+        float x[4][3];
+        int k[4][3];
+        lattice_tet_raw(P, ci, cj, ck, (int)(t % 6), x, k);
+        const double m_t = P.m_tet;
+        if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+        double cen[3];
+        tet_centroid(P, x, k, cen);
+        if (det6_box(P, x, k) == 0.0) {
+            add_mass(P, cen, m_t, cnt, STATS);
+            if (STATS) cnt.u[ST_DEGENERATE]++;
+            continue;
+        }
+        int64_t f0[3], f1[3];
+        fine_range(P, x, k, f0, f1);
+        int64_t cursor = 0;
+        LeafHit hit;
+        double dsum = 0.0;
+        while (next_leaf(P, f0, f1, cursor, hit)) {
+            P3<T> v[4];
+            int base[3];
+            to_grid<T>(P, x, k, bc << hit.level, v, base);
+            TetSetup<T> ts;
+            tet_setup<T>(v, ts);
+            if (!tet_ok(base, ts)) {
+                set_error(P.ws, 4, (int)(t & 0x7fffffff));
+                break;
+            }
+            // cell range of the tetrahedron clipped to this leaf's block (base-cell frame)
+            int lo[3], hi[3], org[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                org[a] = (int)(hit.org[a] - base[a]);
+                lo[a] = ts.lo[a] > org[a] ? ts.lo[a] : org[a];
+                hi[a] = ts.lo[a] + ts.dim[a] - 1 < org[a] + (int)bc - 1 ? ts.lo[a] + ts.dim[a] - 1 : org[a] + (int)bc - 1;
+            }
+            const double rho = 6.0 * m_t / ts.vol6;
+            const bool single = ts.dim[0] == 1 && ts.dim[1] == 1 && ts.dim[2] == 1;
+            const bool g64 = (sizeof(T) == 4) && !(ts.kappa <= P.kappa_max);
+            double* blk = P.out + (int64_t)hit.leaf * bc * bc * bc;
+            for (int cz = lo[2]; cz <= hi[2]; ++cz)
+                for (int cy = lo[1]; cy <= hi[1]; ++cy)
+                    for (int cx = lo[0]; cx <= hi[0]; ++cx) {
+                        if (STATS) cnt.u[ST_BBOX_CELLS]++;
+                        double vol = 0.0;
+                        if (single) {
+                            vol = ts.vol6 / 6.0;
+                            if (STATS) cnt.u[ST_SINGLE_CELL]++;
+                        } else {
+                            const int cls = classify_cell<T>(ts.n, ts.e, ts.pos, ts.neg, (T)cx, (T)cy, (T)cz);
+                            if (cls == CELL_INSIDE) {
+                                vol = 1.0;
+                                if (STATS) cnt.u[ST_INSIDE_CELLS]++;
+                            } else if (cls == CELL_PARTIAL) {
+                                P3<T> p[4];
+#pragma unroll
+                                for (int q = 0; q < 4; ++q)
+                                    p[q] = mk<T>(ts.v[q].x - (T)cx, ts.v[q].y - (T)cy, ts.v[q].z - (T)cz);
+                                if constexpr (sizeof(T) == 4) {
+                                    if (g64) {
+                                        vol = overlap_volume_fp64(p);
+                                        if (STATS) cnt.u[ST_FP64_REDOS]++;
+                                    } else {
+                                        T err;
+                                        vol = (double)overlap_volume<T>(p, ts.n, ts.lx, ts.ly, err);
+                                    }
+                                } else {
+                                    T err;
+                                    vol = (double)overlap_volume<T>(p, ts.n, ts.lx, ts.ly, err);
+                                }
+                                if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
+                            }
+                        }
+                        if (vol > 0.0) {
+                            const double m = rho * vol;
+                            dsum += m;
+                            atomicAdd(blk + (cx - org[0]) + bc * ((cy - org[1]) + bc * (cz - org[2])), m);
+                        }
+                    }
+        }
+        if (sizeof(T) == 4 && P.fixup && m_t != dsum) add_mass(P, cen, m_t - dsum, cnt, STATS);
+    }
+    if (STATS) cnt.flush(P.ws);
+}
+
+// ---------------------------------------------------------------------------
+// warp-cooperative FP32 path: per sub-batch, rounds of (tetrahedron, leaf) pairs
+// ---------------------------------------------------------------------------
+template <bool STATS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    Counters cnt;
+    if (STATS) cnt.zero();
+    const int64_t bc = P.bc;
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(&P.ws->work_counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        if ((int64_t)item >= P.n_items) break;
+        int64_t ci = 0, cj = 0, ck = 0;
+        bool have = false;
+        if (P.src == SRC_LATTICE) {
+            const int64_t segs = (P.nc[0] + 31) / 32;
+            const int64_t row = (int64_t)item / segs, seg = (int64_t)item % segs;
+            const int64_t i = seg * 32 + lane;
+            if (i < P.nc[0]) {
+                ci = i;
+                cj = row % P.nc[1];
+                ck = row / P.nc[1];
+                have = true;
+            }
+        } else {
+            const int64_t u = (int64_t)item * 32 + lane;
+            if (u < P.n_units) {
+                have = cube_of_unit(P, u, ci, cj, ck);
+                if (!have) set_error(P.ws, 3, (int)(u & 0x7fffffff));
+            }
+        }
+        for (int s = 0; s < 6; ++s) {
+            float x[4][3];
+            int k[4][3];
+            double cen[3] = {0.0, 0.0, 0.0};
+            const double m_t = P.m_tet;
+            bool live = false;
+            int64_t f0[3] = {0, 0, 0}, f1[3] = {-1, -1, -1}, cursor = 0;
+            if (have) {
+                lattice_tet_raw(P, ci, cj, ck, s, x, k);
+                tet_centroid(P, x, k, cen);
+                if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+                if (det6_box(P, x, k) == 0.0) {
+                    add_mass(P, cen, m_t, cnt, STATS);
+                    if (STATS) cnt.u[ST_DEGENERATE]++;
+                } else {
+                    fine_range(P, x, k, f0, f1);
+                    live = true;
+                }
+            }
+            double dtot = 0.0;
+            bool more = live;
+            while (__any_sync(kFull, more)) {
+                int npairs = 0;
+                if (more) {
+                    LeafHit hit;
+                    more = next_leaf(P, f0, f1, cursor, hit);
+                    if (more) {
+                        P3<float> v[4];
+                        int base[3];
+                        to_grid<float>(P, x, k, bc << hit.level, v, base);
+                        TetSetup<float> ts;
+                        tet_setup<float>(v, ts);
+                        if (!tet_ok(base, ts)) {
+                            set_error(P.ws, 4, lane);
+                            more = false;
+                        } else {
+                            int lo[3], dim[3];
+#pragma unroll
+                            for (int a = 0; a < 3; ++a) {
+                                const int org = (int)(hit.org[a] - base[a]);
+                                lo[a] = ts.lo[a] > org ? ts.lo[a] : org;
+                                const int hi = ts.lo[a] + ts.dim[a] - 1 < org + (int)bc - 1 ? ts.lo[a] + ts.dim[a] - 1
+                                                                                            : org + (int)bc - 1;
+                                dim[a] = hi - lo[a] + 1;
+                                S->org[a][lane] = org;
+                            }
+                            const int64_t ncell = (int64_t)dim[0] * dim[1] * dim[2];
+                            if (ts.dim[0] == 1 && ts.dim[1] == 1 && ts.dim[2] == 1) {
+                                // whole tetrahedron inside one cell of this leaf
+                                atomicAdd(P.out + (int64_t)hit.leaf * bc * bc * bc + (lo[0] - S->org[0][lane]) +
+                                              bc * ((lo[1] - S->org[1][lane]) + bc * (lo[2] - S->org[2][lane])),
+                                          m_t);
+                                dtot += m_t;
+                                if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; }
+                            } else if (ncell > (int64_t)(1 << 25)) {
+                                set_error(P.ws, 2, lane);
+                            } else if (ncell > 0) {
+                                npairs = (int)ncell;
+                                if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    S->v[3 * q][lane] = ts.v[q].x;
+                                    S->v[3 * q + 1][lane] = ts.v[q].y;
+                                    S->v[3 * q + 2][lane] = ts.v[q].z;
+                                    S->n[3 * q][lane] = ts.n[q].x;
+                                    S->n[3 * q + 1][lane] = ts.n[q].y;
+                                    S->n[3 * q + 2][lane] = ts.n[q].z;
+                                    S->e[q][lane] = ts.e[q];
+                                    S->pos[q][lane] = ts.pos[q];
+                                    S->neg[q][lane] = ts.neg[q];
+                                }
+#pragma unroll
+                                for (int a = 0; a < 3; ++a) {
+                                    S->lo[a][lane] = lo[a];
+                                    S->dim[a][lane] = dim[a];
+                                    S->base[a][lane] = base[a];
+                                }
+                                S->leaf[lane] = hit.leaf;
+                                S->rho[lane] = 6.0 * m_t / ts.vol6;
+                                S->lx[lane] = ts.lx;
+                                S->ly[lane] = ts.ly;
+                                S->guard[lane] = (ts.kappa <= P.kappa_max) ? 0 : 1;
+                            }
+                        }
+                    }
+                }
+                coop_pairs<STATS, true>(P, S, lane, npairs, cnt);
+                if (npairs > 0) dtot += S->dsum[lane];
+                __syncwarp();
+            }
+            if (live && P.fixup && m_t != dtot) add_mass(P, cen, m_t - dtot, cnt, STATS);
+            __syncwarp();
+        }
+    }
+    if (STATS) cnt.flush(P.ws);
+}
+
+// ---------------------------------------------------------------------------
+// octree build: per-level histograms of the tetrahedra's mean edge length
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t hist_offset(int level) { return (int64_t)64 * ((((int64_t)1) << (3 * level)) - 1) / 7; }
+
+__global__ void __launch_bounds__(256) k_tet_size_hist(const DepositParams P, unsigned *__restrict__ hist,
+                                                       double threshold_unused)
+{
+    (void)threshold_unused;
+    __shared__ unsigned sh[64 + 512];  // levels 0 and 1 aggregated per block
+    for (int i = threadIdx.x; i < 576; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t n_tets = 6 * P.n_units;
+    const int levels = P.max_level;  // decisions are made for levels 0 .. max_level-1
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t ci, cj, ck;
+        if (!cube_of_unit(P, t / 6, ci, cj, ck)) continue;
+        float x[4][3];
+        int k[4][3];
+        lattice_tet_raw(P, ci, cj, ck, (int)(t % 6), x, k);
+        double e = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = a + 1; b < 4; ++b) {
+                double s2 = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double d = unwrapped(P, x, k, b, c) - unwrapped(P, x, k, a, c);
+                    s2 += d * d;
+                }
+                e += sqrt(s2);
+            }
+        e /= 6.0;
+        double cen[3];
+        tet_centroid(P, x, k, cen);
+        for (int a = 0; a < 3; ++a) {
+            cen[a] -= P.box * floor(cen[a] / P.box);
+            if (!(cen[a] < P.box)) cen[a] = 0.0;
+        }
+        for (int l = 0; l < levels; ++l) {
+            const int64_t nn = (int64_t)1 << l;
+            int64_t node = 0, stride = 1;
+            for (int a = 0; a < 3; ++a) {
+                int64_t c = (int64_t)floor(cen[a] * (double)nn / P.box);
+                c = c < 0 ? 0 : (c >= nn ? nn - 1 : c);
+                node += c * stride;
+                stride *= nn;
+            }
+            const double h = P.box / ((double)P.bc * (double)nn);
+            const float lg = log10f((float)(e / h));
+            int bin = (int)floorf((lg + 3.0f) * (64.0f / 6.0f));
+            bin = bin < 0 ? 0 : (bin > 63 ? 63 : bin);
+            if (l == 0) atomicAdd(&sh[bin], 1u);
+            else if (l == 1) atomicAdd(&sh[64 + node * 64 + bin], 1u);
+            else atomicAdd(&hist[hist_offset(l) + node * 64 + bin], 1u);
+        }
+    }
+    __syncthreads();
+    const int agg = levels >= 2 ? 576 : (levels == 1 ? 64 : 0);
+    for (int i = threadIdx.x; i < agg; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStream_t st)
+{
+    const int threads = 256;
+    const int64_t n = 6 * p.n_units;
+    int64_t blocks = (n + threads - 1) / threads;
+    const int64_t cap = (int64_t)persistent_blocks((const void *)k_tet_size_hist, threads, 0) * 4;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    k_tet_size_hist<<<(unsigned)blocks, threads, 0, st>>>(p, hist, 0.0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread_per_tet, bool stats,
+                                  int blocks_per_sm, cudaStream_t st)
+{
+    if (thread_per_tet) {
+        const int threads = 128;
+        const void *k = fp64 ? (stats ? (const void *)k_oct_thread<double, true> : (const void *)k_oct_thread<double, false>)
+                             : (stats ? (const void *)k_oct_thread<float, true> : (const void *)k_oct_thread<float, false>);
+        int64_t blocks = (6 * p.n_units + threads - 1) / threads;
+        const int64_t cap = (int64_t)persistent_blocks(k, threads, 0) * 8;
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        void *args[] = {const_cast<DepositParams *>(&p)};
+        return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(threads), args, 0, st);
+    }
+    const int threads = 256;
+    const size_t smem = sizeof(WarpSmem) * (threads / 32);
+    const int minb = (blocks_per_sm >= 2) ? 2 : 1;
+    const void *k = stats ? (minb == 2 ? (const void *)k_oct_warp<true, 2> : (const void *)k_oct_warp<true, 1>)
+                          : (minb == 2 ? (const void *)k_oct_warp<false, 2> : (const void *)k_oct_warp<false, 1>);
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int blocks = persistent_blocks(k, threads, smem);
+    const int64_t need = (p.n_items + 7) / 8;
+    if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
+    void *args[] = {const_cast<DepositParams *>(&p)};
+    return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
+}
+
+}  // namespace pse

@@ -105,3 +105,16 @@ def test_invalid_arguments_return_codes(L):
 def test_workspace_size(L):
     assert L.pse_workspace_size(_lib.PSE_OP_DEPOSIT_UNIFORM, None, None) >= 64
     assert L.pse_workspace_size(12345, None, None) == 0
+
+
+def test_octree_leaf_validation_needs_no_gpu(L):
+    import numpy as np
+    st = _lib.Octree()
+    bad = np.array([[1, 0, 0, 0]], np.int32)  # one octant does not tile the box
+    rc = L.pse_octree_from_leaves(bad.ctypes.data_as(ctypes.c_void_p), 1, 4, 1, 1.0, ctypes.byref(st))
+    assert rc == _lib.PSE_ERR_INVALID_ARG and "tile" in L.pse_last_error().decode()
+    ovl = np.array([[0, 0, 0, 0], [1, 0, 0, 0]], np.int32)
+    rc = L.pse_octree_from_leaves(ovl.ctypes.data_as(ctypes.c_void_p), 2, 4, 1, 1.0, ctypes.byref(st))
+    assert rc == _lib.PSE_ERR_INVALID_ARG and "overlap" in L.pse_last_error().decode()
+    rc = L.pse_octree_from_leaves(bad.ctypes.data_as(ctypes.c_void_p), 1, 0, 1, 1.0, ctypes.byref(st))
+    assert rc == _lib.PSE_ERR_INVALID_ARG
