@@ -99,8 +99,9 @@ typedef struct pse_deposit_opts {
                                 estimated relative error of its FP32 clip exceeds guard_eps (<=0: default) */
     int64_t spin_limit;      /* iteration bound of every device-side wait (<=0: default) */
     int32_t accumulate;      /* 0: the call overwrites the output; 1: it adds to it */
-    int32_t mass_fixup;      /* FP32 path: 1 adds each tetrahedron's rounding residual m_t - sum(deposits)
-                                to the cell of its centroid, so total mass is conserved to float64 rounding */
+    int32_t mass_fixup;      /* FP32 path with accumulate = 0: 1 rescales the call's output by
+                                sum(m_t) / sum(computed deposits), so total mass is conserved to float64
+                                rounding (every cell moves by the same relative ~1e-8) */
     const int64_t *d_cube_ids; /* NULL: every cube; else deposit only these Lagrangian cubes (device int64
                                   [n_cube_ids], each in [0, number of cubes); n_cube_ids may be 0) */
     int64_t n_cube_ids;

@@ -47,7 +47,7 @@ pse_deposit_opts default_opts()
 
 // FP32 guard: a tetrahedron whose conditioning estimate kappa (total face area x longest
 // edge / |6V|; about 8 for an undistorted Kuhn tetrahedron) exceeds kappa_max is clipped
-// in float64.  kappa_max = 4e6 * guard_eps (40 by default): measured against the FP64
+// in float64.  kappa_max = 3.2e6 * guard_eps (32 by default): measured against the FP64
 // oracle on shell-crossed Zel'dovich and jittered lattices, FP32 clips of tetrahedra
 // below this bound keep the per-cell error (relative, floored at 1e-3 of the mean cell
 // mass) below guard_eps.
@@ -59,7 +59,7 @@ constexpr int kDefaultBlocksPerSm = 1;
 float kappa_limit(double guard_eps)
 {
     const double g = guard_eps > 0.0 ? guard_eps : kDefaultGuardEps;
-    return (float)(4.0e6 * g);
+    return (float)(3.2e6 * g);
 }
 
 struct WsLease {
@@ -136,7 +136,10 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
     if (rc != PSE_OK) return rc;
     p.ws = lease.ws;
     p.kappa_max = kappa_limit(o.guard_eps);
-    p.fixup = o.mass_fixup ? 1 : 0;
+    // FP32 mass renormalisation: the call's deposits are scaled by sum(m_t)/sum(deposits);
+    // it needs the output to hold this call's deposits only (accumulate = 0)
+    const bool renorm = o.mass_fixup && !o.accumulate && o.precision == PSE_FP32_FP64ACC;
+    p.fixup = renorm ? 1 : 0;
     cudaError_t e;
     if (!o.accumulate) {
         e = cudaMemsetAsync(p.out, 0, (size_t)cells * sizeof(double), st);
@@ -160,6 +163,10 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
             e = pse::launch_warp_coop(p, stats, bps, st);
         }
         if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+    }
+    if (renorm && p.n_units > 0) {
+        e = pse::launch_scale(p.out, cells, p.ws, st);
+        if (e != cudaSuccess) return cuda_fail(e, "mass renormalisation launch");
     }
     if (stats) {
         pse::Workspace hw;

@@ -182,12 +182,31 @@ __device__ __forceinline__ int size_bin(int64_t cells)
 struct Counters {
     unsigned long long u[ST_NUM_U64];
     double mass_in, dropped;
+    double tgt, dep;  // always kept: sum of m_t and of every computed deposit (renormalisation)
     __device__ void zero()
     {
 #pragma unroll
         for (int i = 0; i < ST_NUM_U64; ++i) u[i] = 0;
         mass_in = 0.0;
         dropped = 0.0;
+    }
+    __device__ void zero_mass()
+    {
+        tgt = 0.0;
+        dep = 0.0;
+    }
+    __device__ void flush_mass(Workspace *ws)
+    {
+        double a = tgt, b = dep;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(kFull, a, o);
+            b += __shfl_down_sync(kFull, b, o);
+        }
+        if ((threadIdx.x & 31) == 0 && (a != 0.0 || b != 0.0)) {
+            atomicAdd(&ws->mass_target, a);
+            atomicAdd(&ws->mass_deposited, b);
+        }
     }
     __device__ void flush(Workspace *ws)
     {
@@ -230,7 +249,6 @@ struct WarpSmem {
     int leaf[32];         // octree: leaf of this (tetrahedron, leaf) pair
     int org[3][32];       // octree: the leaf's first cell, base-cell frame
     double rho[32];
-    double dsum[32];      // FP64 sum of what each tetrahedron deposited
     int start[32];        // exclusive prefix of the pair counts
     int guard[32];        // 1: clip this tetrahedron in float64
     unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
@@ -252,21 +270,6 @@ __device__ __forceinline__ void decompose(int local, int dx, int dy, int &ix, in
     const int r = local - iz * dxy;
     iy = r / dx;
     ix = r - iy * dx;
-}
-
-// Adds each lane's v into S->dsum[key] when the lanes holding the same key are
-// contiguous (key < 0: no contribution): a segmented reduction to the first lane of
-// each run, which then updates the shared sum without atomics.
-__device__ __forceinline__ void segmented_add(WarpSmem *S, int lane, int key, double v)
-{
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_down_sync(kFull, v, o);
-        const int k2 = __shfl_down_sync(kFull, key, o);
-        if (lane + o < 32 && k2 == key) v += y;
-    }
-    const int kp = __shfl_up_sync(kFull, key, 1);
-    if (key >= 0 && (lane == 0 || kp != key)) S->dsum[key] += v;
 }
 
 // The float64 redo of a guarded clip, kept out of line so that the FP32 hot loop
@@ -302,8 +305,6 @@ __device__ __forceinline__ bool deposit_pair(const DepositParams &P, const WarpS
 template <bool STATS, bool OCT>
 __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
 {
-    int key = -1;
-    double m = 0.0;
     if (lane < count) {
         const unsigned long long ent = S->q[lane];
         const int t = (int)(ent & 31u);
@@ -328,20 +329,18 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
             if (STATS) cnt.u[ST_FP64_REDOS]++;
         }
         if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
-        key = t;
         if (vol > 0.0) {
-            m = S->rho[t] * vol;
+            const double m = S->rho[t] * vol;
+            cnt.dep += m;
             if (!deposit_pair<OCT>(P, S, t, cx, cy, cz, m) && STATS) cnt.dropped += m;
         }
     }
-    if (P.fixup) segmented_add(S, lane, key, m);
     __syncwarp();
 }
 
 // Enumerate every (virtual tetrahedron, cell) pair of the 32 records in S (npairs:
 // this lane's pair count), 32 pairs per round: classify; deposit "cell inside"
-// pairs; queue partial pairs and clip them 32 at a time.  On return S->dsum[lane]
-// holds the float64 sum of what this lane's record deposited.
+// pairs; queue partial pairs and clip them 32 at a time.
 template <bool STATS, bool OCT>
 __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, int lane, int npairs, Counters &cnt)
 {
@@ -354,15 +353,12 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
     }
     const int total = __shfl_sync(kFull, incl, 31);
     S->start[lane] = incl - npairs;
-    S->dsum[lane] = 0.0;
     __syncwarp();
     int qn = 0;
     for (int b0 = 0; b0 < total; b0 += 32) {
         const int idx = b0 + lane;
         bool partial = false;
         unsigned long long ent = 0;
-        int ikey = -1;
-        double im = 0.0;
         if (idx < total) {
             int t = 0;
 #pragma unroll
@@ -383,19 +379,17 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                 ng[f] = S->neg[f][t];
             }
             const int cls = classify_cell<float>(n, e, ps, ng, cx, cy, cz);
-            ikey = t;  // every valid lane carries its tetrahedron, so each one's lanes form one run
             if (cls == CELL_INSIDE) {
                 const double m = S->rho[t];
+                cnt.dep += m;
                 if (!deposit_pair<OCT>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) && STATS)
                     cnt.dropped += m;
-                im = m;
                 if (STATS) cnt.u[ST_INSIDE_CELLS]++;
             } else if (cls == CELL_PARTIAL) {
                 partial = true;
                 ent = q_pack(t, ix, iy, iz);
             }
         }
-        if (P.fixup && __any_sync(kFull, im != 0.0)) segmented_add(S, lane, ikey, im);
         const unsigned bal = __ballot_sync(kFull, partial);
         if (partial) S->q[qn + __popc(bal & lt_mask)] = ent;
         qn += __popc(bal);

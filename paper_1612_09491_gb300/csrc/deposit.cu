@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
 {
     Counters cnt;
     if (STATS) cnt.zero();
+    cnt.zero_mass();
     const int64_t n_tets = (P.src == SRC_TETS) ? P.n_units : 6 * P.n_units;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -53,10 +54,12 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
             set_error(P.ws, 4, (int)(t & 0x7fffffff));
             continue;
         }
+        cnt.tgt += m_t;
         if (ts.vol6 == 0.0) {
             int c[3];
             centroid_cell(ts.v, c);
             if (!deposit_cell(P, base[0] + c[0], base[1] + c[1], base[2] + c[2], m_t) && STATS) cnt.dropped += m_t;
+            cnt.dep += m_t;
             if (STATS) cnt.u[ST_DEGENERATE]++;
             continue;
         }
@@ -65,13 +68,13 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
         if (ncell == 1) {
             if (!deposit_cell(P, base[0] + ts.lo[0], base[1] + ts.lo[1], base[2] + ts.lo[2], m_t) && STATS)
                 cnt.dropped += m_t;
+            cnt.dep += m_t;
             if (STATS) cnt.u[ST_SINGLE_CELL]++;
             continue;
         }
         const double rho = 6.0 * m_t / ts.vol6;
         // FP32 guard: ill-conditioned tetrahedra are clipped in float64
         const bool g64 = (sizeof(T) == 4) && !(ts.kappa <= P.kappa_max);
-        double dsum = 0.0;
         for (int iz = 0; iz < ts.dim[2]; ++iz)
             for (int iy = 0; iy < ts.dim[1]; ++iy)
                 for (int ix = 0; ix < ts.dim[0]; ++ix) {
@@ -101,22 +104,15 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                     }
                     if (vol > 0.0) {
                         const double m = rho * vol;
-                        dsum += m;
+                        cnt.dep += m;
                         if (!deposit_cell(P, (int64_t)base[0] + cx, (int64_t)base[1] + cy, (int64_t)base[2] + cz, m) &&
                             STATS)
                             cnt.dropped += m;
                     }
                 }
-        // FP32 path: the rounding residual of this tetrahedron's mass goes to its centroid cell
-        if (sizeof(T) == 4 && P.fixup && m_t != dsum) {
-            int c[3];
-            centroid_cell(ts.v, c);
-            if (!deposit_cell(P, (int64_t)base[0] + c[0], (int64_t)base[1] + c[1], (int64_t)base[2] + c[2], m_t - dsum) &&
-                STATS)
-                cnt.dropped += m_t - dsum;
-        }
     }
     if (STATS) cnt.flush(P.ws);
+    if (P.fixup) cnt.flush_mass(P.ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -130,6 +126,7 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
     const int lane = threadIdx.x & 31;
     Counters cnt;
     if (STATS) cnt.zero();
+    cnt.zero_mass();
     const int nsub = (P.src == SRC_TETS) ? 1 : 6;
 
     for (;;) {
@@ -167,7 +164,6 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
             // ---- 1. one tetrahedron per lane
             int npairs = 0;
             double m_t = 0.0;
-            bool coop = false;
             if (unit >= 0) {
                 P3<float> v[4];
                 int base[3];
@@ -190,17 +186,21 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
                     if (!deposit_cell(P, (int64_t)base[0] + c[0], (int64_t)base[1] + c[1], (int64_t)base[2] + c[2], m_t) &&
                         STATS)
                         cnt.dropped += m_t;
+                    cnt.tgt += m_t;
+                    cnt.dep += m_t;
                     if (STATS) cnt.u[ST_DEGENERATE]++;
                 } else if (ncell == 1) {
                     if (!deposit_cell(P, (int64_t)base[0] + ts.lo[0], (int64_t)base[1] + ts.lo[1],
                                       (int64_t)base[2] + ts.lo[2], m_t) && STATS)
                         cnt.dropped += m_t;
+                    cnt.tgt += m_t;
+                    cnt.dep += m_t;
                     if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
                 } else if (ncell > (int64_t)(1 << 25)) {
                     set_error(P.ws, 2, lane);  // 32 x 2^25 pairs still fit the int32 scan
                 } else {
-                    coop = true;
                     npairs = (int)ncell;
+                    cnt.tgt += m_t;
                     if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -228,24 +228,23 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
             }
             // ---- 2. pair enumeration and clips
             coop_pairs<STATS, false>(P, S, lane, npairs, cnt);
-            // ---- 3. mass residual of each tetrahedron to its centroid cell
-            if (coop && P.fixup) {
-                const double resid = m_t - S->dsum[lane];
-                if (resid != 0.0) {
-                    P3<float> vv[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) vv[q] = mk<float>(S->v[3 * q][lane], S->v[3 * q + 1][lane], S->v[3 * q + 2][lane]);
-                    int c[3];
-                    centroid_cell(vv, c);
-                    if (!deposit_cell(P, (int64_t)S->base[0][lane] + c[0], (int64_t)S->base[1][lane] + c[1],
-                                      (int64_t)S->base[2][lane] + c[2], resid) && STATS)
-                        cnt.dropped += resid;
-                }
-            }
             __syncwarp();
         }
     }
     if (STATS) cnt.flush(P.ws);
+    if (P.fixup) cnt.flush_mass(P.ws);
+}
+
+// ---------------------------------------------------------------------------
+// mass renormalisation of an FP32 deposit: out *= (sum of m_t) / (sum of deposits)
+// ---------------------------------------------------------------------------
+__global__ void k_scale(double *__restrict__ out, long long n, const Workspace *__restrict__ ws)
+{
+    const double dep = ws->mass_deposited;
+    if (!(dep > 0.0)) return;
+    const double f = ws->mass_target / dep;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] *= f;
 }
 
 // ---------------------------------------------------------------------------
@@ -333,6 +332,16 @@ cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_
     if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
     void *args[] = {const_cast<DepositParams *>(&p)};
     return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
+}
+
+cudaError_t launch_scale(double *out, int64_t n, const Workspace *ws, cudaStream_t st)
+{
+    const int threads = 256;
+    int64_t blocks = (n + threads - 1) / threads;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    k_scale<<<(unsigned)blocks, threads, 0, st>>>(out, n, ws);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_build_tets(const float *pos, const int64_t n[3], const int64_t nc[3], int periodic, double box,

@@ -151,91 +151,114 @@ PSE_HD P3<T> pick4(const P3<T> (&p)[4], int i)
 }
 
 // ---------------------------------------------------------------------------
-// Sutherland-Hodgman clip of an edge-list polygon against the plane x_AX = s,
-// keeping x_AX >= s (UP = false) or x_AX < s (UP = true).  Slots [0, NE) hold the
-// current edges (a -> b); the edge the clip creates on the plane (exit -> entry)
-// goes to slot NE.  Dropped edges collapse onto the local origin (zero length).
+// Polygon clipping on an edge list (slots of directed edges a -> b; the polygon
+// stays a closed chain; dropped edges collapse onto the local origin).  A slab pass
+// clips against the two parallel planes lo <= c < hi of one axis at once and appends
+// the two edges it creates on them (exit -> entry).  Classification uses a rounding
+// tolerance: a coordinate within tol of a plane counts as lying on it (on lo: inside;
+// on hi: outside), so a polygon that is convex up to rounding crosses each plane at
+// most twice.  Every edge is processed without branches.
 // ---------------------------------------------------------------------------
-template <class T, int AX, bool UP, int NE>
-PSE_HD void clip_plane(P3<T> (&A)[9], P3<T> (&B)[9], T s, T tol)
+template <class T>
+PSE_HD T coord(const P3<T> &p, int ax)
 {
-    const P3<T> z0 = mk<T>(T(0), T(0), T(0));
-    P3<T> ex = z0, en = z0;
-#pragma unroll
-    for (int k = 0; k < NE; ++k) {
-        // coordinates within rounding distance of the plane are put on it, so that a
-        // polygon that is convex up to rounding crosses the plane at most twice
-        if (fabs(get<AX>(A[k]) - s) <= tol) put<AX>(A[k], s);
-        if (fabs(get<AX>(B[k]) - s) <= tol) put<AX>(B[k], s);
-        const T ca = get<AX>(A[k]), cb = get<AX>(B[k]);
-        const bool ia = UP ? (ca < s) : (ca >= s);
-        const bool ib = UP ? (cb < s) : (cb >= s);
-        if (ia != ib) {
-            const T t = fdiv(s - ca, cb - ca);
-            P3<T> I = mk<T>(fmaT(t, B[k].x - A[k].x, A[k].x), fmaT(t, B[k].y - A[k].y, A[k].y),
-                            fmaT(t, B[k].z - A[k].z, A[k].z));
-            put<AX>(I, s);
-            if (ia) { B[k] = I; ex = I; } else { A[k] = I; en = I; }
-        } else if (!ia) {
-            A[k] = z0;
-            B[k] = z0;
-        }
-    }
-    A[NE] = ex;
-    B[NE] = en;
+    return ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
 }
 
+// point of edge a -> b at parameter t, with coordinate `ax` set exactly to s
+template <class T>
+PSE_HD P3<T> at_plane(const P3<T> &a, const P3<T> &b, T t, int ax, T s)
+{
+    P3<T> r = mk<T>(fmaT(t, b.x - a.x, a.x), fmaT(t, b.y - a.y, a.y), fmaT(t, b.z - a.z, a.z));
+    r.x = (ax == 0) ? s : r.x;
+    r.y = (ax == 1) ? s : r.y;
+    r.z = (ax == 2) ? s : r.z;
+    return r;
+}
+
+// Clip slots [0, NE) against lo <= c_ax < hi; new edges go to slots NE (on lo) and NE+1 (on hi).
 template <class T, int NE>
-PSE_HD void collapse_slot(P3<T> (&A)[9], P3<T> (&B)[9])
-{
-    A[NE] = mk<T>(T(0), T(0), T(0));
-    B[NE] = A[NE];
-}
-
-// Split the edge-list polygon at z = s.  The kept part (z >= s if KEEP_ABOVE, else
-// z < s) stays in slots [0, NE) with its new edge in slot NE; the other part is
-// integrated on the fly: returns 6 * ∫∫ (s - l(x,y)) dx dy over its projection
-// (fan from the local origin), l(x,y) = l0 + lx x + ly y.
-template <class T, int NE, bool KEEP_ABOVE>
-PSE_HD T split_z(P3<T> (&A)[9], P3<T> (&B)[9], T s, T tol, T l0, T lx, T ly)
+PSE_HD void clip_slab(P3<T> (&A)[9], P3<T> (&B)[9], int ax, T lo, T hi, T tol)
 {
     const P3<T> z0 = mk<T>(T(0), T(0), T(0));
-    P3<T> ex = z0, en = z0;
-    bool got = false;
-    T acc = T(0);
-    const T fo = s - l0;  // integrand at the anchor (the local origin)
+    P3<T> xl = z0, nl = z0, xh = z0, nh = z0;  // exit / entry points on lo and on hi
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
-        if (fabs(A[k].z - s) <= tol) A[k].z = s;
-        if (fabs(B[k].z - s) <= tol) B[k].z = s;
-        const T ca = A[k].z, cb = B[k].z;
-        const bool ia = KEEP_ABOVE ? (ca >= s) : (ca < s);
-        const bool ib = KEEP_ABOVE ? (cb >= s) : (cb < s);
-        P3<T> oa = A[k], ob = B[k];  // the part of the edge on the other side
-        bool off = !ia || !ib;
-        if (ia != ib) {
-            const T t = fdiv(s - ca, cb - ca);
-            const P3<T> I = mk<T>(fmaT(t, B[k].x - A[k].x, A[k].x), fmaT(t, B[k].y - A[k].y, A[k].y), s);
-            if (ia) { oa = I; B[k] = I; ex = I; } else { ob = I; A[k] = I; en = I; }
-            got = true;
-        } else if (!ia) {
-            A[k] = z0;
-            B[k] = z0;
-        }
-        if (off) {
-            const T fa = s - fmaT(lx, oa.x, fmaT(ly, oa.y, l0));
-            const T fb = s - fmaT(lx, ob.x, fmaT(ly, ob.y, l0));
-            acc = fmaT(cross_xy(oa, ob), fo + fa + fb, acc);
-        }
+        const P3<T> a = A[k], b = B[k];
+        const T ca = coord(a, ax), cb = coord(b, ax);
+        const bool a_lo = ca < lo - tol, b_lo = cb < lo - tol;   // below the slab
+        const bool a_hi = ca >= hi - tol, b_hi = cb >= hi - tol; // above the slab (on hi counts as above)
+        const T inv = fdiv(T(1), cb - ca);
+        const P3<T> pl = at_plane(a, b, (lo - ca) * inv, ax, lo);
+        const P3<T> ph = at_plane(a, b, (hi - ca) * inv, ax, hi);
+        const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
+        P3<T> na = a_lo ? pl : (a_hi ? ph : a);
+        P3<T> nb = b_lo ? pl : (b_hi ? ph : b);
+        na = drop ? z0 : na;
+        nb = drop ? z0 : nb;
+        A[k] = na;
+        B[k] = nb;
+        xl = (!a_lo && b_lo) ? pl : xl;
+        nl = (a_lo && !b_lo) ? pl : nl;
+        xh = (!a_hi && b_hi) ? ph : xh;
+        nh = (a_hi && !b_hi) ? ph : nh;
     }
-    A[NE] = ex;
-    B[NE] = en;
-    if (got) {  // closing edge of the other part: entry -> exit
-        const T fa = s - fmaT(lx, en.x, fmaT(ly, en.y, l0));
-        const T fb = s - fmaT(lx, ex.x, fmaT(ly, ex.y, l0));
-        acc = fmaT(cross_xy(en, ex), fo + fa + fb, acc);
+    A[NE] = xl;
+    B[NE] = nl;
+    A[NE + 1] = xh;
+    B[NE + 1] = nh;
+}
+
+// 6 * ∫∫ (s - l(x,y)) dx dy over the projection of segment-fan (a, b) from the local origin
+template <class T>
+PSE_HD T fan_const(const P3<T> &a, const P3<T> &b, T s, T l0, T lx, T ly)
+{
+    const T fa = s - fmaT(lx, a.x, fmaT(ly, a.y, l0));
+    const T fb = s - fmaT(lx, b.x, fmaT(ly, b.y, l0));
+    return cross_xy(a, b) * ((s - l0) + fa + fb);
+}
+
+// Split slots [0, NE) at z = lo and z = hi: the part in between stays (new edges in slots
+// NE, NE+1); the parts below and above are integrated on the fly (fan from the local
+// origin, integrands lo - l and hi - l).  Returns 6 * their integral.
+template <class T, int NE>
+PSE_HD T split_zslab(P3<T> (&A)[9], P3<T> (&B)[9], T lo, T hi, T tol, T l0, T lx, T ly, T &mag)
+{
+    const P3<T> z0 = mk<T>(T(0), T(0), T(0));
+    P3<T> xl = z0, nl = z0, xh = z0, nh = z0;
+    T below = T(0), above = T(0);
+#pragma unroll
+    for (int k = 0; k < NE; ++k) {
+        const P3<T> a = A[k], b = B[k];
+        const bool a_lo = a.z < lo - tol, b_lo = b.z < lo - tol;
+        const bool a_hi = a.z >= hi - tol, b_hi = b.z >= hi - tol;
+        const T inv = fdiv(T(1), b.z - a.z);
+        const P3<T> pl = at_plane(a, b, (lo - a.z) * inv, 2, lo);
+        const P3<T> ph = at_plane(a, b, (hi - a.z) * inv, 2, hi);
+        // the part below lo: whole edge, or from an endpoint to pl
+        const P3<T> ba = a_lo ? a : pl, bb = b_lo ? b : pl;
+        below += (a_lo || b_lo) ? fan_const(ba, bb, lo, l0, lx, ly) : T(0);
+        const P3<T> ua = a_hi ? a : ph, ub = b_hi ? b : ph;
+        above += (a_hi || b_hi) ? fan_const(ua, ub, hi, l0, lx, ly) : T(0);
+        const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
+        P3<T> na = a_lo ? pl : (a_hi ? ph : a);
+        P3<T> nb = b_lo ? pl : (b_hi ? ph : b);
+        A[k] = drop ? z0 : na;
+        B[k] = drop ? z0 : nb;
+        xl = (!a_lo && b_lo) ? pl : xl;
+        nl = (a_lo && !b_lo) ? pl : nl;
+        xh = (!a_hi && b_hi) ? ph : xh;
+        nh = (a_hi && !b_hi) ? ph : nh;
     }
-    return acc;
+    A[NE] = xl;
+    B[NE] = nl;
+    A[NE + 1] = xh;
+    B[NE + 1] = nh;
+    // closing edges of the parts below (entry -> exit on lo) and above (on hi)
+    below += fan_const(nl, xl, lo, l0, lx, ly);
+    above += fan_const(nh, xh, hi, l0, lx, ly);
+    mag += fabs(below) + fabs(above);
+    return below + above;
 }
 
 // ---------------------------------------------------------------------------
@@ -276,26 +299,22 @@ PSE_HD T overlap_volume(const P3<T> (&p)[4], const P3<T> (&n)[4], T lx, T ly, T 
         const P3<T> nf = (f == 0) ? n[0] : (f == 1) ? n[1] : (f == 2) ? n[2] : n[3];
         if (nf.z == T(0)) continue;  // vertical face: no projected area
         const T mnz = fmin(a.z, fmin(b.z, c.z)), mxz = fmax(a.z, fmax(b.z, c.z));
-        // snapping distance: a few units of rounding of this face's coordinates
+        // classification tolerance: a few units of rounding of this face's coordinates
         const T cmag = fmax(T(1), fmax(fmax(fmax(fabs(mnx), fabs(mxx)), fmax(fabs(mny), fabs(mxy))),
                                        fmax(fabs(mnz), fabs(mxz))));
         const T tol = T(8) * std::numeric_limits<T>::epsilon() * cmag;
         // anchor of the between-planes region: the local origin projected onto the face plane
-        const T n2 = dot(nf, nf);
-        const T sc = fdiv(dot(nf, a), n2);
+        const T sc = fdiv(dot(nf, a), dot(nf, nf));
         const P3<T> o = mk<T>(sc * nf.x, sc * nf.y, sc * nf.z);
 
         P3<T> A[9], B[9];
         A[0] = a; B[0] = b;
         A[1] = b; B[1] = c;
         A[2] = c; B[2] = a;
-        if (mnx < xlo) clip_plane<T, 0, false, 3>(A, B, xlo, tol); else collapse_slot<T, 3>(A, B);
-        if (mxx >= xhi) clip_plane<T, 0, true, 4>(A, B, xhi, tol); else collapse_slot<T, 4>(A, B);
-        if (mny < ylo) clip_plane<T, 1, false, 5>(A, B, ylo, tol); else collapse_slot<T, 5>(A, B);
-        if (mxy >= yhi) clip_plane<T, 1, true, 6>(A, B, yhi, tol); else collapse_slot<T, 6>(A, B);
-        T below = T(0), above = T(0);
-        if (mnz < zlo) below = split_z<T, 7, true>(A, B, zlo, tol, l0, lx, ly); else collapse_slot<T, 7>(A, B);
-        if (mxz >= zhi) above = split_z<T, 8, false>(A, B, zhi, tol, l0, lx, ly); else collapse_slot<T, 8>(A, B);
+        A[3] = B[3] = A[4] = B[4] = mk<T>(T(0), T(0), T(0));
+        clip_slab<T, 3>(A, B, 0, xlo, xhi, tol);
+        clip_slab<T, 5>(A, B, 1, ylo, yhi, tol);
+        T outside = split_zslab<T, 7>(A, B, zlo, zhi, tol, l0, lx, ly, mag);
         // between the planes: integrand z - l, fan from o
         const T fo = o.z - fmaT(lx, o.x, fmaT(ly, o.y, l0));
         T mid = T(0);
@@ -305,8 +324,8 @@ PSE_HD T overlap_volume(const P3<T> (&p)[4], const P3<T> (&n)[4], T lx, T ly, T 
             const T fb = B[k].z - fmaT(lx, B[k].x, fmaT(ly, B[k].y, l0));
             mid = fmaT(cross_xy(sub(A[k], o), sub(B[k], o)), fo + fa + fb, mid);
         }
-        vol += (below + above) + mid;
-        mag += fabs(below) + fabs(above) + fabs(mid);
+        vol += outside + mid;
+        mag += fabs(mid);
     }
     err = mag * T(1.0 / 6.0);
     return vol * T(1.0 / 6.0);

@@ -28,6 +28,8 @@ struct Workspace {
     unsigned long long stats[ST_NUM_U64];
     double mass_in;
     double mass_dropped;
+    double mass_target;     // sum of m_t over processed tetrahedra (FP32 mass renormalisation)
+    double mass_deposited;  // sum of every computed deposit, in the grid or dropped
     int error_code;                    // first device-side error (0 = none)
     int error_detail;
 };
@@ -55,7 +57,7 @@ struct DepositParams {
     double *out;
     // numerics
     float kappa_max;           // FP32 path: tetrahedra with kappa above this clip in float64
-    int32_t fixup;
+    int32_t fixup;             // accumulate mass_target / mass_deposited for the renormalisation
     // octree target (deposit onto leaf blocks)
     int32_t bc;                // cells per leaf block side
     int32_t max_level;
@@ -73,6 +75,7 @@ cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_
 cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStream_t st);
 cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread_per_tet, bool stats,
                                   int blocks_per_sm, cudaStream_t st);
+cudaError_t launch_scale(double *out, int64_t n, const Workspace *ws, cudaStream_t st);
 cudaError_t launch_build_tets(const float *pos, const int64_t n[3], const int64_t nc[3], int periodic,
                               double box, int32_t *vidx, float *vol, int64_t n_tets, cudaStream_t st);
 

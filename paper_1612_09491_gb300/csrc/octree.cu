@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
 {
     Counters cnt;
     if (STATS) cnt.zero();
+    cnt.zero_mass();
     const int64_t n_tets = 6 * P.n_units;
     const int64_t bc = P.bc;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
@@ -223,10 +224,12 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
         lattice_tet_raw(P, ci, cj, ck, (int)(t % 6), x, k);
         const double m_t = P.m_tet;
         if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+        cnt.tgt += m_t;
         double cen[3];
         tet_centroid(P, x, k, cen);
         if (det6_box(P, x, k) == 0.0) {
             add_mass(P, cen, m_t, cnt, STATS);
+            cnt.dep += m_t;
             if (STATS) cnt.u[ST_DEGENERATE]++;
             continue;
         }
@@ -234,7 +237,6 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
         fine_range(P, x, k, f0, f1);
         int64_t cursor = 0;
         LeafHit hit;
-        double dsum = 0.0;
         while (next_leaf(P, f0, f1, cursor, hit)) {
             P3<T> v[4];
             int base[3];
@@ -292,14 +294,14 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
                         }
                         if (vol > 0.0) {
                             const double m = rho * vol;
-                            dsum += m;
+                            cnt.dep += m;
                             atomicAdd(blk + (cx - org[0]) + bc * ((cy - org[1]) + bc * (cz - org[2])), m);
                         }
                     }
         }
-        if (sizeof(T) == 4 && P.fixup && m_t != dsum) add_mass(P, cen, m_t - dsum, cnt, STATS);
     }
     if (STATS) cnt.flush(P.ws);
+    if (P.fixup) cnt.flush_mass(P.ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -313,6 +315,7 @@ __global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
     const int lane = threadIdx.x & 31;
     Counters cnt;
     if (STATS) cnt.zero();
+    cnt.zero_mass();
     const int64_t bc = P.bc;
 
     for (;;) {
@@ -350,15 +353,16 @@ __global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
                 lattice_tet_raw(P, ci, cj, ck, s, x, k);
                 tet_centroid(P, x, k, cen);
                 if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+                cnt.tgt += m_t;
                 if (det6_box(P, x, k) == 0.0) {
                     add_mass(P, cen, m_t, cnt, STATS);
+                    cnt.dep += m_t;
                     if (STATS) cnt.u[ST_DEGENERATE]++;
                 } else {
                     fine_range(P, x, k, f0, f1);
                     live = true;
                 }
             }
-            double dtot = 0.0;
             bool more = live;
             while (__any_sync(kFull, more)) {
                 int npairs = 0;
@@ -391,7 +395,7 @@ __global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
                                 atomicAdd(P.out + (int64_t)hit.leaf * bc * bc * bc + (lo[0] - S->org[0][lane]) +
                                               bc * ((lo[1] - S->org[1][lane]) + bc * (lo[2] - S->org[2][lane])),
                                           m_t);
-                                dtot += m_t;
+                                cnt.dep += m_t;
                                 if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; }
                             } else if (ncell > (int64_t)(1 << 25)) {
                                 set_error(P.ws, 2, lane);
@@ -426,14 +430,13 @@ __global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
                     }
                 }
                 coop_pairs<STATS, true>(P, S, lane, npairs, cnt);
-                if (npairs > 0) dtot += S->dsum[lane];
                 __syncwarp();
             }
-            if (live && P.fixup && m_t != dtot) add_mass(P, cen, m_t - dtot, cnt, STATS);
             __syncwarp();
         }
     }
     if (STATS) cnt.flush(P.ws);
+    if (P.fixup) cnt.flush_mass(P.ws);
 }
 
 // ---------------------------------------------------------------------------
