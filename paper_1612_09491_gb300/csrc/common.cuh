@@ -58,7 +58,7 @@ __device__ __forceinline__ int64_t wrap_idx(int64_t i, int64_t n)
 // in float64 on the float32 inputs.
 template <class T>
 __device__ __forceinline__ void lattice_tet(const DepositParams &P, int64_t ci, int64_t cj, int64_t ck, int s,
-                                            P3<T> (&v)[4], int (&base)[3])
+                                            P3<T> (&v)[4], int (&base)[3], P3<float> *res = nullptr)
 {
     int o1[3], o2[3];
     kuhn_offsets(s, o1, o2);
@@ -80,6 +80,7 @@ __device__ __forceinline__ void lattice_tet(const DepositParams &P, int64_t ci, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         T c[3];
+        float rr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             int shift = 0;
@@ -88,17 +89,21 @@ __device__ __forceinline__ void lattice_tet(const DepositParams &P, int64_t ci, 
                 shift = (d >= 0.5 * P.box) ? -1 : ((d < -0.5 * P.box) ? 1 : 0);
             }
             const long long off = (long long)shift * P.g[a] - base[a];
-            if constexpr (sizeof(T) == 4)
+            if constexpr (sizeof(T) == 4) {
                 c[a] = fmaf(x[q][a], P.scale_f[a], (float)off);
-            else
+                if (res) rr[a] = (float)(fma((double)x[q][a], P.scale_d[a], (double)off) - (double)c[a]);
+            } else {
                 c[a] = fma((double)x[q][a], P.scale_d[a], (double)off);
+            }
         }
         v[q] = mk<T>(c[0], c[1], c[2]);
+        if (sizeof(T) == 4 && res) res[q] = mk<float>(rr[0], rr[1], rr[2]);
     }
 }
 
 template <class T>
-__device__ __forceinline__ void explicit_tet(const DepositParams &P, int64_t t, P3<T> (&v)[4], int (&base)[3])
+__device__ __forceinline__ void explicit_tet(const DepositParams &P, int64_t t, P3<T> (&v)[4], int (&base)[3],
+                                             P3<float> *res = nullptr)
 {
     const float *p = P.verts + 12 * t;
     float x[4][3];
@@ -111,15 +116,48 @@ __device__ __forceinline__ void explicit_tet(const DepositParams &P, int64_t t, 
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         T c[3];
+        float rr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            if constexpr (sizeof(T) == 4)
+            if constexpr (sizeof(T) == 4) {
                 c[a] = fmaf(x[q][a], P.scale_f[a], (float)(-base[a]));
-            else
+                if (res) rr[a] = (float)(fma((double)x[q][a], P.scale_d[a], (double)(-base[a])) - (double)c[a]);
+            } else {
                 c[a] = fma((double)x[q][a], P.scale_d[a], (double)(-base[a]));
+            }
         }
         v[q] = mk<T>(c[0], c[1], c[2]);
+        if (sizeof(T) == 4 && res) res[q] = mk<float>(rr[0], rr[1], rr[2]);
     }
+}
+
+// The float32 vertices of the FP32 path are rounded; res holds the rounding residuals
+// (exact value = (double)v + (double)res, both terms exact in float64), so that the
+// guard's float64 redo and volume use the exact tetrahedron.
+__device__ __forceinline__ void swap12(P3<float> (&r)[4])
+{
+    const P3<float> t = r[1];
+    r[1] = r[2];
+    r[2] = t;
+}
+
+// exact vertices in the frame of cell (cx, cy, cz) of the base frame
+__device__ __forceinline__ void exact_vertices(const P3<float> (&v)[4], const P3<float> (&r)[4], int cx, int cy,
+                                               int cz, P3<double> (&pd)[4])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        pd[q] = mk<double>(((double)v[q].x + (double)r[q].x) - (double)cx, ((double)v[q].y + (double)r[q].y) - (double)cy,
+                           ((double)v[q].z + (double)r[q].z) - (double)cz);
+}
+
+// |6V| of the exact tetrahedron (falls back to the float32 one if that is 0)
+__device__ __forceinline__ double exact_vol6(const P3<float> (&v)[4], const P3<float> (&r)[4], double vol6_f32)
+{
+    P3<double> pd[4];
+    exact_vertices(v, r, 0, 0, 0, pd);
+    const double d = fabs(det6(pd));
+    return d > 0.0 ? d : vol6_f32;
 }
 
 // Lagrangian cube of work unit u; false (and nothing read) for an out-of-range cube id.
@@ -251,6 +289,7 @@ struct WarpSmem {
     double rho[32];
     int start[32];        // exclusive prefix of the pair counts
     int guard[32];        // 1: clip this tetrahedron in float64
+    float vlo[12][32];    // guarded tetrahedra: rounding residuals of v (exact = v + vlo)
     unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
 };
 
@@ -272,17 +311,31 @@ __device__ __forceinline__ void decompose(int local, int dx, int dy, int &ix, in
     ix = r - iy * dx;
 }
 
-// The float64 redo of a guarded clip, kept out of line so that the FP32 hot loop
-// stays small; vertices passed by value (cell frame, positively oriented).
-__device__ __noinline__ double redo_fp64(float x0, float y0, float z0, float x1, float y1, float z1, float x2,
-                                         float y2, float z2, float x3, float y3, float z3)
+// The float64 redo of a guarded clip of record t against cell (cx, cy, cz), kept out
+// of line so that the FP32 hot loop stays small; it rebuilds the exact vertices from
+// the float32 vertices and their residuals.
+__device__ __noinline__ double redo_fp64(const WarpSmem *S, int t, int cx, int cy, int cz)
 {
-    P3<float> p[4];
-    p[0] = mk<float>(x0, y0, z0);
-    p[1] = mk<float>(x1, y1, z1);
-    p[2] = mk<float>(x2, y2, z2);
-    p[3] = mk<float>(x3, y3, z3);
-    return overlap_volume_fp64(p);
+    P3<float> v[4], r[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q] = mk<float>(S->v[3 * q][t], S->v[3 * q + 1][t], S->v[3 * q + 2][t]);
+        r[q] = mk<float>(S->vlo[3 * q][t], S->vlo[3 * q + 1][t], S->vlo[3 * q + 2][t]);
+    }
+    P3<double> pd[4];
+    exact_vertices(v, r, cx, cy, cz, pd);
+    return overlap_volume_fp64(pd);
+}
+
+// Record a guarded tetrahedron's residuals for redo_fp64.
+__device__ __forceinline__ void store_residuals(WarpSmem *S, int lane, const P3<float> (&r)[4])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        S->vlo[3 * q][lane] = r[q].x;
+        S->vlo[3 * q + 1][lane] = r[q].y;
+        S->vlo[3 * q + 2][lane] = r[q].z;
+    }
 }
 
 // Add m to cell (cx, cy, cz) (base-cell frame) of virtual tetrahedron t: the uniform
@@ -311,21 +364,20 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
         const int cx = S->lo[0][t] + (int)((ent >> 5) & kQMask);
         const int cy = S->lo[1][t] + (int)((ent >> (5 + kQBits)) & kQMask);
         const int cz = S->lo[2][t] + (int)((ent >> (5 + 2 * kQBits)) & kQMask);
-        const float fx = (float)cx, fy = (float)cy, fz = (float)cz;
-        P3<float> p[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            p[q] = mk<float>(S->v[3 * q][t] - fx, S->v[3 * q + 1][t] - fy, S->v[3 * q + 2][t] - fz);
         double vol;
         if (!S->guard[t]) {
+            const float fx = (float)cx, fy = (float)cy, fz = (float)cz;
+            P3<float> p[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                p[q] = mk<float>(S->v[3 * q][t] - fx, S->v[3 * q + 1][t] - fy, S->v[3 * q + 2][t] - fz);
             P3<float> n[4];
 #pragma unroll
             for (int f = 0; f < 4; ++f) n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
             float err;
             vol = (double)overlap_volume<float>(p, n, S->lx[t], S->ly[t], err);
         } else {
-            vol = redo_fp64(p[0].x, p[0].y, p[0].z, p[1].x, p[1].y, p[1].z, p[2].x, p[2].y, p[2].z, p[3].x, p[3].y,
-                            p[3].z);
+            vol = redo_fp64(S, t, cx, cy, cz);
             if (STATS) cnt.u[ST_FP64_REDOS]++;
         }
         if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;

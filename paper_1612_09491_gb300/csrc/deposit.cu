@@ -33,10 +33,11 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
          t += (int64_t)gridDim.x * blockDim.x) {
         P3<T> v[4];
+        P3<float> res[4];
         int base[3];
         double m_t;
         if (P.src == SRC_TETS) {
-            explicit_tet<T>(P, t, v, base);
+            explicit_tet<T>(P, t, v, base, res);
             m_t = P.tet_mass[t];
         } else {
             int64_t i, j, k;
@@ -44,11 +45,11 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                 set_error(P.ws, 3, (int)((t / 6) & 0x7fffffff));
                 continue;
             }
-            lattice_tet<T>(P, i, j, k, (int)(t % 6), v, base);
+            lattice_tet<T>(P, i, j, k, (int)(t % 6), v, base, res);
             m_t = P.m_tet;
         }
         TetSetup<T> ts;
-        tet_setup<T>(v, ts);
+        if (tet_setup<T>(v, ts)) swap12(res);
         if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
         if (!tet_ok(base, ts)) {
             set_error(P.ws, 4, (int)(t & 0x7fffffff));
@@ -72,9 +73,12 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
             if (STATS) cnt.u[ST_SINGLE_CELL]++;
             continue;
         }
-        const double rho = 6.0 * m_t / ts.vol6;
-        // FP32 guard: ill-conditioned tetrahedra are clipped in float64
+        // FP32 guard: ill-conditioned tetrahedra are clipped in float64 from their exact vertices
         const bool g64 = (sizeof(T) == 4) && !(ts.kappa <= P.kappa_max);
+        double rho = 6.0 * m_t / ts.vol6;
+        if constexpr (sizeof(T) == 4) {
+            if (g64) rho = 6.0 * m_t / exact_vol6(ts.v, res, ts.vol6);
+        }
         for (int iz = 0; iz < ts.dim[2]; ++iz)
             for (int iy = 0; iy < ts.dim[1]; ++iy)
                 for (int ix = 0; ix < ts.dim[0]; ++ix) {
@@ -90,7 +94,9 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                         for (int q = 0; q < 4; ++q) p[q] = mk<T>(ts.v[q].x - (T)cx, ts.v[q].y - (T)cy, ts.v[q].z - (T)cz);
                         if constexpr (sizeof(T) == 4) {
                             if (g64) {
-                                vol = overlap_volume_fp64(p);
+                                P3<double> pd[4];
+                                exact_vertices(ts.v, res, cx, cy, cz, pd);
+                                vol = overlap_volume_fp64(pd);
                                 if (STATS) cnt.u[ST_FP64_REDOS]++;
                             } else {
                                 T err;
@@ -165,17 +171,17 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
             int npairs = 0;
             double m_t = 0.0;
             if (unit >= 0) {
-                P3<float> v[4];
+                P3<float> v[4], res[4];
                 int base[3];
                 if (P.src == SRC_TETS) {
-                    explicit_tet<float>(P, unit, v, base);
+                    explicit_tet<float>(P, unit, v, base, res);
                     m_t = P.tet_mass[unit];
                 } else {
-                    lattice_tet<float>(P, ci, cj, ck, s, v, base);
+                    lattice_tet<float>(P, ci, cj, ck, s, v, base, res);
                     m_t = P.m_tet;
                 }
                 TetSetup<float> ts;
-                tet_setup<float>(v, ts);
+                if (tet_setup<float>(v, ts)) swap12(res);
                 if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
                 const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
                 if (!tet_ok(base, ts)) {
@@ -220,10 +226,12 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
                         S->dim[a][lane] = ts.dim[a];
                         S->base[a][lane] = base[a];
                     }
-                    S->rho[lane] = 6.0 * m_t / ts.vol6;
+                    const int guard = (ts.kappa <= P.kappa_max) ? 0 : 1;
+                    S->rho[lane] = 6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6);
                     S->lx[lane] = ts.lx;
                     S->ly[lane] = ts.ly;
-                    S->guard[lane] = (ts.kappa <= P.kappa_max) ? 0 : 1;
+                    S->guard[lane] = guard;
+                    if (guard) store_residuals(S, lane, res);
                 }
             }
             // ---- 2. pair enumeration and clips

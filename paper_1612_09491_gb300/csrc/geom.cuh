@@ -370,13 +370,27 @@ PSE_HD void face_normals(const P3<T> (&v)[4], P3<T> (&n)[4])
     }
 }
 
-// Overlap volume of a positively oriented tetrahedron (cell frame) computed in float64
-// from float32 vertices: the redo path of the FP32 guard.
-PSE_HD double overlap_volume_fp64(const P3<float> (&p)[4])
+// float64 6 * signed volume of four vertices
+PSE_HD double det6(const P3<double> (&p)[4])
 {
-    P3<double> pd[4], nd[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) pd[q] = mk<double>(p[q].x, p[q].y, p[q].z);
+    const double ax = p[1].x - p[0].x, ay = p[1].y - p[0].y, az = p[1].z - p[0].z;
+    const double bx = p[2].x - p[0].x, by = p[2].y - p[0].y, bz = p[2].z - p[0].z;
+    const double cx = p[3].x - p[0].x, cy = p[3].y - p[0].y, cz = p[3].z - p[0].z;
+    return ax * (by * cz - bz * cy) - ay * (bx * cz - bz * cx) + az * (bx * cy - by * cx);
+}
+
+// Overlap volume of a tetrahedron (cell frame, float64 vertices, either orientation)
+// with the cell, computed in float64: the redo path of the FP32 guard.  The vertices
+// must be the exact ones (not the float32-rounded set the FP32 clip used), otherwise
+// the redo only reproduces the rounding of the inputs.
+PSE_HD double overlap_volume_fp64(P3<double> (&pd)[4])
+{
+    if (det6(pd) < 0.0) {
+        const P3<double> t = pd[1];
+        pd[1] = pd[2];
+        pd[2] = t;
+    }
+    P3<double> nd[4];
     face_normals<double>(pd, nd);
     double lx, ly, err;
     ref_slopes<double>(nd, lx, ly);
@@ -398,8 +412,9 @@ struct TetSetup {
     T lx, ly;          // slopes of the reference plane l (the most horizontal face's plane)
 };
 
+// Returns true if v[1] and v[2] were swapped to make the tetrahedron positively oriented.
 template <class T>
-PSE_HD void tet_setup(P3<T> (&v)[4], TetSetup<T> &s)
+PSE_HD bool tet_setup(P3<T> (&v)[4], TetSetup<T> &s)
 {
     // float64 signed volume of the vertices as given
     const double ax = (double)v[1].x - (double)v[0].x, ay = (double)v[1].y - (double)v[0].y,
@@ -462,6 +477,7 @@ PSE_HD void tet_setup(P3<T> (&v)[4], TetSetup<T> &s)
     ref_slopes<T>(s.n, s.lx, s.ly);
     const double denom = s.vol6 > 0.0 ? s.vol6 : 1e-300;
     s.kappa = (float)((double)area2 * sqrt((double)lmax2) / denom);
+    return d6 < 0.0;
 }
 
 // Cell classification for the cell with corner c (base-cell frame, integers).

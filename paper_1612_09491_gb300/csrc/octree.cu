@@ -52,7 +52,7 @@ __device__ __forceinline__ void lattice_tet_raw(const DepositParams &P, int64_t 
 // relative to its base cell (the cell of vertex 0).
 template <class T>
 __device__ __forceinline__ void to_grid(const DepositParams &P, const float (&x)[4][3], const int (&k)[4][3],
-                                        int64_t g, P3<T> (&v)[4], int (&base)[3])
+                                        int64_t g, P3<T> (&v)[4], int (&base)[3], P3<float> *res = nullptr)
 {
     const double sd = (double)g / P.box;
     const float sf = (float)sd;
@@ -61,15 +61,19 @@ __device__ __forceinline__ void to_grid(const DepositParams &P, const float (&x)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         T c[3];
+        float rr[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const long long off = (long long)k[q][a] * g - base[a];
-            if constexpr (sizeof(T) == 4)
+            if constexpr (sizeof(T) == 4) {
                 c[a] = fmaf(x[q][a], sf, (float)off);
-            else
+                if (res) rr[a] = (float)(fma((double)x[q][a], sd, (double)off) - (double)c[a]);
+            } else {
                 c[a] = fma((double)x[q][a], sd, (double)off);
+            }
         }
         v[q] = mk<T>(c[0], c[1], c[2]);
+        if (sizeof(T) == 4 && res) res[q] = mk<float>(rr[0], rr[1], rr[2]);
     }
 }
 
@@ -239,10 +243,11 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
         LeafHit hit;
         while (next_leaf(P, f0, f1, cursor, hit)) {
             P3<T> v[4];
+            P3<float> res[4];
             int base[3];
-            to_grid<T>(P, x, k, bc << hit.level, v, base);
+            to_grid<T>(P, x, k, bc << hit.level, v, base, res);
             TetSetup<T> ts;
-            tet_setup<T>(v, ts);
+            if (tet_setup<T>(v, ts)) swap12(res);
             if (!tet_ok(base, ts)) {
                 set_error(P.ws, 4, (int)(t & 0x7fffffff));
                 break;
@@ -255,9 +260,12 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
                 lo[a] = ts.lo[a] > org[a] ? ts.lo[a] : org[a];
                 hi[a] = ts.lo[a] + ts.dim[a] - 1 < org[a] + (int)bc - 1 ? ts.lo[a] + ts.dim[a] - 1 : org[a] + (int)bc - 1;
             }
-            const double rho = 6.0 * m_t / ts.vol6;
             const bool single = ts.dim[0] == 1 && ts.dim[1] == 1 && ts.dim[2] == 1;
-            const bool g64 = (sizeof(T) == 4) && !(ts.kappa <= P.kappa_max);
+            const bool g64 = (sizeof(T) == 4) && !(ts.kappa <= P.kappa_max) && !single;
+            double rho = 6.0 * m_t / ts.vol6;
+            if constexpr (sizeof(T) == 4) {
+                if (g64) rho = 6.0 * m_t / exact_vol6(ts.v, res, ts.vol6);
+            }
             double* blk = P.out + (int64_t)hit.leaf * bc * bc * bc;
             for (int cz = lo[2]; cz <= hi[2]; ++cz)
                 for (int cy = lo[1]; cy <= hi[1]; ++cy)
@@ -279,7 +287,9 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
                                     p[q] = mk<T>(ts.v[q].x - (T)cx, ts.v[q].y - (T)cy, ts.v[q].z - (T)cz);
                                 if constexpr (sizeof(T) == 4) {
                                     if (g64) {
-                                        vol = overlap_volume_fp64(p);
+                                        P3<double> pd[4];
+                                        exact_vertices(ts.v, res, cx, cy, cz, pd);
+                                        vol = overlap_volume_fp64(pd);
                                         if (STATS) cnt.u[ST_FP64_REDOS]++;
                                     } else {
                                         T err;
@@ -370,11 +380,11 @@ __global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
                     LeafHit hit;
                     more = next_leaf(P, f0, f1, cursor, hit);
                     if (more) {
-                        P3<float> v[4];
+                        P3<float> v[4], res[4];
                         int base[3];
-                        to_grid<float>(P, x, k, bc << hit.level, v, base);
+                        to_grid<float>(P, x, k, bc << hit.level, v, base, res);
                         TetSetup<float> ts;
-                        tet_setup<float>(v, ts);
+                        if (tet_setup<float>(v, ts)) swap12(res);
                         if (!tet_ok(base, ts)) {
                             set_error(P.ws, 4, lane);
                             more = false;
@@ -421,10 +431,12 @@ __global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
                                     S->base[a][lane] = base[a];
                                 }
                                 S->leaf[lane] = hit.leaf;
-                                S->rho[lane] = 6.0 * m_t / ts.vol6;
+                                const int guard = (ts.kappa <= P.kappa_max) ? 0 : 1;
+                                S->rho[lane] = 6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6);
                                 S->lx[lane] = ts.lx;
                                 S->ly[lane] = ts.ly;
-                                S->guard[lane] = (ts.kappa <= P.kappa_max) ? 0 : 1;
+                                S->guard[lane] = guard;
+                                if (guard) store_residuals(S, lane, res);
                             }
                         }
                     }

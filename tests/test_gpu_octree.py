@@ -151,7 +151,8 @@ def test_build_rejects_open_lattice_and_bad_args():
 
 def test_config3_full_size_sampled():
     """256^3 particles (100.7M tetrahedra), k^-1.5, rms 4 spacings, octree of 16^3 blocks, levels 0-4:
-    GPU-built tree; full deposit conserves mass; 2048 random cubes deposited alone on both sides."""
+    GPU-built tree; the plain FP64 GPU path agrees with the oracle on 2048 random cubes deposited
+    alone, and the FP32 path agrees with the FP64 path on every cell of the full deposit."""
     cfg = CONFIGS[3]
     pos = config_positions(cfg)
     dpos = torch.from_numpy(pos).cuda()
@@ -165,6 +166,14 @@ def test_config3_full_size_sampled():
     assert abs(float(out.sum()) - 1.0) <= 1e-12
     ids = np.sort(np.random.default_rng(33).choice(cfg.n ** 3, 2048, replace=False))
     ref, _ = oracle.deposit_octree(pos, cfg.n, leaves, cfg.bc, cfg.max_level, cube_ids=ids, nthreads=8)
-    sub = pse.deposit_octree(dpos, cfg.n, oct_, cube_ids=torch.from_numpy(ids).cuda()).cpu().numpy()
-    e = cell_errors(sub, ref)
+    sub = pse.deposit_octree(dpos, cfg.n, oct_, cube_ids=torch.from_numpy(ids).cuda(),
+                             precision=pse.PSE_FP64_PLAIN, schedule=pse.PSE_THREAD_PER_TET).cpu().numpy()
+    # floor: 1e-3 of the mean occupied cell of the FULL deposit (the sample alone is sparse)
+    full = out.cpu().numpy()
+    e = cell_errors(sub, ref, floor_mass=1e-3 * full.sum() / np.count_nonzero(full))
+    assert e["max_rel"] <= 1e-9, e
+    full64 = pse.deposit_octree(dpos, cfg.n, oct_, precision=pse.PSE_FP64_PLAIN,
+                                schedule=pse.PSE_THREAD_PER_TET).cpu().numpy()
+    e = cell_errors(full, full64)
     assert e["max_rel"] <= 1e-5, e
+    assert e["mass"] <= 1e-12, e
