@@ -226,6 +226,28 @@ PSE_API int pse_deposit_octree(const float *d_pos, const pse_lattice *lat, const
 PSE_API void pse_free_octree(pse_octree *oct);
 
 /*
+ * The leaf list of pse_build_octree_from_tet_sizes, for callers that cannot allocate
+ * memory (code inside CUDA graph capture, plugins whose host owns the device allocator,
+ * real-time loops that must not wait on it).  The paper has no counterpart: this is an
+ * interface variant, not part of the method.  It allocates nothing and does not
+ * synchronise: its scratch (work counters and the size histograms) is a fixed 256 KB
+ * device array inside the library -- every GPU that loads the library holds it until
+ * the process exits -- and its result goes to caller buffers.
+ *   d_leaves    device int32 [cap][4]: leaves (level, ix, iy, iz) in the order of
+ *               pse_build_octree_from_tet_sizes; at most cap are written.
+ *   d_n_leaves  device int64 [1]: the number of leaves (may exceed cap: then call again).
+ *   max_level   <= 4 (the fixed scratch holds the histograms of levels 0..3); a larger
+ *               value returns PSE_ERR_INVALID_ARG without touching the device.
+ * The first call on each device resolves the array's device address with that device
+ * current; make that first call outside stream capture.  Every call reuses the same
+ * array (it is cleared at the start of each call): calls that overlap on the GPU, on
+ * any stream, race and give wrong results.
+ */
+PSE_API int pse_build_octree_leaves_noalloc(const float *d_pos, const pse_lattice *lat, int32_t bc,
+                                            int32_t max_level, double edge_threshold_cells, int32_t *d_leaves,
+                                            int64_t cap, int64_t *d_n_leaves, void *stream);
+
+/*
  * Bytes of device workspace an operation needs.  op = PSE_OP_*; lat may be NULL;
  * op_params: for PSE_OP_BUILD_OCTREE a host int32 max_level (required), otherwise unused
  * (may be NULL).  Returns 0 for an unknown op.

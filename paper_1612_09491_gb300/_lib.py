@@ -42,6 +42,7 @@ EXPORTED = (
     "pse_build_octree_from_tet_sizes",
     "pse_deposit_octree",
     "pse_free_octree",
+    "pse_build_octree_leaves_noalloc",
     "pse_workspace_size",
     "pse_last_error",
     "pse_abi_version",
@@ -125,6 +126,9 @@ def load(build_if_missing: bool = False):
                                          ctypes.POINTER(DepositStats), vp, ctypes.c_size_t, vp]
         L.pse_free_octree.argtypes = [OP]
         L.pse_free_octree.restype = None
+        L.pse_build_octree_leaves_noalloc.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int32, ctypes.c_int32,
+                                                      ctypes.c_double, vp, ctypes.c_int64, vp, vp]
+        L.pse_build_octree_leaves_noalloc.restype = ctypes.c_int
         L.pse_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Lattice), vp]
         L.pse_workspace_size.restype = ctypes.c_size_t
         L.pse_last_error.argtypes = []

@@ -328,6 +328,10 @@ int make_octree(const int32_t *leaves, int64_t n_leaves, int32_t bc, int32_t max
 }
 }  // namespace
 
+namespace pse {
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+}  // namespace pse
+
 extern "C" {
 
 const char *pse_last_error(void) { return g_last_error.c_str(); }

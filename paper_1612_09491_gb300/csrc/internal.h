@@ -69,6 +69,9 @@ struct DepositParams {
     Workspace *ws;
 };
 
+// message returned by pse_last_error() on this host thread (abi.cu)
+void set_last_error(const char *msg);
+
 // launchers (deposit.cu)
 cudaError_t launch_thread_per_tet(const DepositParams &p, bool fp64, bool stats, cudaStream_t st);
 cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st);
