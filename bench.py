@@ -223,23 +223,28 @@ def main():
     pos_host = config_positions(cfg)
     pos = torch.from_numpy(pos_host).to(dev)
     out = torch.empty((g, g, g), dtype=torch.float64, device=dev)
-    ws = torch.empty(pse.workspace_size(), dtype=torch.uint8, device=dev)
+    ws = torch.empty(pse.workspace_size(schedule=pse.PSE_BINNED_PERSISTENT), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     from paper_1612_09491_gb300 import autotune
-    tuned, tune_ms = autotune.tune(
-        lambda tu: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=pse.PSE_FP32_FP64ACC,
-                                       schedule=pse.PSE_WARP_COOPERATIVE, tuning=tu),
-        signature=f"uniform:{cfg.name}")
+
+    def call(tu, **kw):
+        """One deposit with an autotuner candidate {"schedule": "warp" | "binned", knobs...}."""
+        knobs = {k: v for k, v in tu.items() if k != "schedule"}
+        sched = pse.PSE_BINNED_PERSISTENT if tu["schedule"] == "binned" else pse.PSE_WARP_COOPERATIVE
+        return pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=pse.PSE_FP32_FP64ACC,
+                                   schedule=sched, tuning=knobs, **kw)
+
+    tuned, tune_ms = autotune.tune(call, signature=f"uniform:{cfg.name}", candidates=autotune.UNIFORM_CANDIDATES)
 
     def step(accumulate=False):
-        pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=pse.PSE_FP32_FP64ACC,
-                            schedule=pse.PSE_WARP_COOPERATIVE, accumulate=accumulate, tuning=tuned)
+        call(tuned, accumulate=accumulate)
 
+    # kernels of one step: [bin pass, chunk scan,] deposit kernel, mass renormalisation
+    launches_per_step = 4 if tuned["schedule"] == "binned" else 2
     # counters of one pass (synchronising call, outside the timed region)
-    _, st = pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=pse.PSE_FP32_FP64ACC,
-                                schedule=pse.PSE_WARP_COOPERATIVE, stats=True)
+    _, st = call(tuned, stats=True)
     fast_grid = out.cpu().numpy().copy()
 
     for _ in range(args.warmup):
@@ -336,7 +341,8 @@ def main():
             "config": {"workload": cfg.name, "particles": f"{n}^3", "tets": n_tets, "grid": f"uniform {g}^3 float64",
                        "spectrum": f"P(k)~k^{cfg.spectral_index}", "rms_disp_spacings": cfg.rms_disp,
                        "precision": "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up",
-                       "schedule": "warp-cooperative", "tuning": tuned, "autotune_ms": tune_ms,
+                       "schedule": {"binned": "binned persistent", "warp": "warp-cooperative"}[tuned["schedule"]],
+                       "tuning": tuned, "autotune_ms": tune_ms,
                        "l2": "512 MB buffer written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "clips_per_s": clips_per_s,
@@ -351,7 +357,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": world * n_tets / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(pos_host.nbytes),
                     "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": e2e_ms},
-            "gpu_launches": args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "clocks": csum,
             "wall_s_timed": t_wall,
         }

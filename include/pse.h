@@ -74,7 +74,10 @@ extern "C" {
 /* schedule (pse_deposit_opts.schedule) */
 #define PSE_THREAD_PER_TET 0    /* one thread per tetrahedron (the plain baseline) */
 #define PSE_WARP_COOPERATIVE 1  /* one warp per batch of tetrahedra, lanes over (tet, cell) pairs */
-#define PSE_BINNED_PERSISTENT 2 /* size-binned persistent kernel (bins from bbox count or cost model) */
+#define PSE_BINNED_PERSISTENT 2 /* size-binned persistent kernel: a bin pass queues every tetrahedron whose
+                                   bounding box exceeds pse_tuning.split_cells; one persistent kernel
+                                   takes work items (pieces of the queued tetrahedra first, then rows of
+                                   cubes) from one atomic counter.  FP32 path, uniform grids. */
 
 /* operation ids for pse_workspace_size */
 #define PSE_OP_DEPOSIT_UNIFORM 1
@@ -93,7 +96,10 @@ typedef struct pse_lattice {
 typedef struct pse_deposit_opts {
     int32_t precision;       /* PSE_FP64_PLAIN or PSE_FP32_FP64ACC */
     int32_t schedule;        /* PSE_THREAD_PER_TET, PSE_WARP_COOPERATIVE or PSE_BINNED_PERSISTENT */
-    const void *cost_model;  /* nullable device pointer to trained cost-model weights (binned schedule) */
+    const void *cost_model;  /* nullable device cost model (pse_costmodel_*): the binned schedule then splits
+                                the tetrahedra whose predicted partial clips exceed split_cells, instead
+                                of those whose bounding box exceeds split_cells cells (lattice deposits
+                                need pse_workspace_size(PSE_OP_DEPOSIT_UNIFORM, lat, opts) bytes) */
     const void *tuning;      /* nullable host pointer to a pse_tuning block; NULL = built-in defaults */
     double guard_eps;        /* FP32 clip guard: redo a tetrahedron's clips in float64 when the
                                 estimated relative error of its FP32 clip exceeds guard_eps (<=0: default) */
@@ -140,11 +146,15 @@ typedef struct pse_octree {
 } pse_octree;
 
 typedef struct pse_tuning {
-    int32_t blocks_per_sm;   /* resident blocks per SM of the warp-cooperative kernel: 1 (no register
+    int32_t blocks_per_sm;   /* resident blocks per SM of the warp-cooperative kernels: 1 (no register
                                 cap) or 2 (128 registers per thread); <= 0: the built-in default */
-    int32_t warps_per_block;
-    int32_t bin_edges[7];    /* bbox-cell-count upper edges of bins 0..6 (bin 7 is the rest) */
-    int32_t reserved;
+    int32_t warps_per_block; /* reserved (8) */
+    int32_t split_cells;     /* binned schedule: a tetrahedron whose bounding box has more cells than
+                                this is split across warps; <= 0: default 1024 */
+    int32_t chunk_cells;     /* binned schedule: bounding-box cells per split work item; <= 0: default 512 */
+    int32_t use_graph;       /* binned schedule with a caller workspace: 1 = replay the call's launch
+                                sequence as a CUDA graph (captured once per distinct argument set) */
+    int32_t reserved[5];
 } pse_tuning;
 
 /*
@@ -169,8 +179,13 @@ PSE_API int pse_build_tets_from_lagrangian_grid(const float *d_pos, const pse_la
  *   d_cell_mass float64 [g0*g1*g2] device, written (accumulate = 0) or added to.
  *   opts        nullable: NULL = PSE_FP32_FP64ACC, PSE_WARP_COOPERATIVE, overwrite, mass fix-up on.
  *   h_stats     nullable host: filled with counters; when non-null the call synchronises.
- *   d_ws        device workspace of ws_bytes >= pse_workspace_size(PSE_OP_DEPOSIT_UNIFORM, lat, grid_n);
- *               NULL with ws_bytes = 0 makes the library allocate it stream-ordered for this call.
+ *   d_ws        device workspace (16-byte aligned) of ws_bytes >= pse_workspace_size(
+ *               PSE_OP_DEPOSIT_UNIFORM, lat, opts); NULL with ws_bytes = 0 makes the library
+ *               allocate it stream-ordered for this call.
+ * Device-side failures (a bad cube id, non-finite coordinates, a bounding box beyond
+ * the int32 cell range) are recorded in the workspace and returned as PSE_ERR_DEVICE
+ * by calls that pass h_stats; calls without h_stats do not synchronise and do not
+ * report them.
  */
 PSE_API int pse_deposit_uniform(const float *d_pos, const pse_lattice *lat, const int64_t grid_n[3],
                         double *d_cell_mass, const pse_deposit_opts *opts, pse_deposit_stats *h_stats,
@@ -248,9 +263,60 @@ PSE_API int pse_build_octree_leaves_noalloc(const float *d_pos, const pse_lattic
                                             int64_t cap, int64_t *d_n_leaves, void *stream);
 
 /*
+ * Learned cost model of the binned schedule (the paper has none: it balances work by
+ * estimated cost per tetrahedron, Sec. 5, and notes the spread of work, Sec. 6.2).
+ * A model is a caller-owned, 16-byte aligned device buffer of pse_costmodel_bytes().
+ * Its parameters are a float32 vector of PSE_COSTMODEL_NPARAMS values:
+ *   mu[16], sigma[16]        feature standardisation z = (f - mu) / sigma
+ *   W1[64][16], b1[64]       ReLU layer
+ *   W2[64][64], b2[64]       ReLU layer
+ *   W3[2][64], b3[2]         outputs: log(1 + overlapped cells), log(1 + partial clips)
+ * The forward pass rounds z, the weights and the hidden activations to bfloat16 and
+ * accumulates in float32 (tensor cores for prediction).  The model only decides which
+ * tetrahedra the binned schedule splits; deposited values never depend on it.
+ */
+#define PSE_COSTMODEL_NFEAT 16
+#define PSE_COSTMODEL_NPARAMS 5410
+#define PSE_TRAIN_FP32 1      /* train step in float32 without bfloat16 rounding (gradient checks) */
+#define PSE_TRAIN_GRAD_ONLY 2 /* compute the gradient (readable with pse_costmodel_get) but do not update */
+
+PSE_API size_t pse_costmodel_bytes(void);
+/* Upload parameters (host float32 [PSE_COSTMODEL_NPARAMS]); resets the optimiser state.
+ * Synchronises `stream`.  PSE_ERR_INVALID_ARG if a sigma is not finite and > 0. */
+PSE_API int pse_costmodel_set(void *d_model, const float *h_params, void *stream);
+/* Download parameters and/or the last training step's gradient (host float32
+ * [PSE_COSTMODEL_NPARAMS] each, nullable; the gradient of mu and sigma is 0).  Synchronises. */
+PSE_API int pse_costmodel_get(const void *d_model, float *h_params, float *h_grad, void *stream);
+/* Features of every lattice tetrahedron (id 6 * cube + s) on the grid grid_n:
+ * d_feat float32 [T][16], T = 6 * cubes.  The features are, in grid units: bounding-box
+ * extent (3), offset of its low corner in its cell (3), log2 bounding-box cells,
+ * log2 volume, log2 surface area, longest / shortest / mean edge, log2 max(kappa, 1),
+ * volume over bounding-box volume, log2 longest over shortest edge, cube root of the
+ * volume over the mean edge.  Asynchronous. */
+PSE_API int pse_costmodel_features(const float *d_pos, const pse_lattice *lat, const int64_t grid_n[3],
+                                   float *d_feat, void *stream);
+/* Labels from the exact deposit: d_counts int32 [T][2] = (cells whose overlap exceeds
+ * 1e-6 of the cell volume, partial clips) of every lattice tetrahedron on grid grid_n, from the same
+ * classification and FP32 clip (FP64 guard at guard_eps, <= 0: default) as
+ * pse_deposit_uniform.  Nothing is deposited.  Asynchronous. */
+PSE_API int pse_tet_counts(const float *d_pos, const pse_lattice *lat, const int64_t grid_n[3], double guard_eps,
+                           int32_t *d_counts, void *stream);
+/* Predictions d_out float32 [n][2] for features d_feat float32 [n][16].  Asynchronous. */
+PSE_API int pse_costmodel_predict(const void *d_model, const float *d_feat, int64_t n, float *d_out, void *stream);
+/* One Adam step (lr; beta 0.9 / 0.999, eps 1e-8) on the mean squared error
+ * (1 / 2B) sum (y - target)^2 of a batch of B rows of d_feat float32 [*][16] and
+ * d_target float32 [*][2]: rows d_index[0..B) (device int64, nullable = rows 0..B).
+ * d_loss (device float64 [1]) receives the loss before the update.  flags:
+ * PSE_TRAIN_FP32, PSE_TRAIN_GRAD_ONLY.  Asynchronous. */
+PSE_API int pse_costmodel_train_step(void *d_model, const float *d_feat, const float *d_target,
+                                     const int64_t *d_index, int64_t batch, float lr, int32_t flags, double *d_loss,
+                                     void *stream);
+
+/*
  * Bytes of device workspace an operation needs.  op = PSE_OP_*; lat may be NULL;
- * op_params: for PSE_OP_BUILD_OCTREE a host int32 max_level (required), otherwise unused
- * (may be NULL).  Returns 0 for an unknown op.
+ * op_params: for PSE_OP_BUILD_OCTREE a host int32 max_level (required); for the deposit
+ * ops a nullable host pse_deposit_opts (the binned schedule needs room for its queue).
+ * Returns 0 for an unknown op.
  */
 PSE_API size_t pse_workspace_size(int op, const pse_lattice *lat, const void *op_params);
 

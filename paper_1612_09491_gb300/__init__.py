@@ -66,12 +66,19 @@ _keep = []  # tuning blocks referenced by option structs during a call
 
 
 def opts(precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
-         accumulate: bool = False, mass_fixup: bool = True, cube_ids=None, tuning=None) -> _lib.DepositOpts:
+         accumulate: bool = False, mass_fixup: bool = True, cube_ids=None, tuning=None,
+         cost_model=None) -> _lib.DepositOpts:
+    """cost_model: a costmodel.CostModel (binned schedule) or None."""
     o = _lib.DepositOpts()
+    if cost_model is not None:
+        o.cost_model = cost_model.ptr
     if tuning is not None:
         tu = _lib.Tuning()
         tu.blocks_per_sm = int(tuning.get("blocks_per_sm", 0))
         tu.warps_per_block = int(tuning.get("warps_per_block", 0))
+        tu.split_cells = int(tuning.get("split_cells", 0))
+        tu.chunk_cells = int(tuning.get("chunk_cells", 0))
+        tu.use_graph = int(tuning.get("use_graph", 0))
         _keep[:] = [tu]
         o.tuning = ctypes.cast(ctypes.pointer(tu), ctypes.c_void_p).value
     o.precision = precision
@@ -95,7 +102,7 @@ def _grid3(grid_n):
 def deposit_uniform(pos, n, grid_n, *, box: float = 1.0, periodic: bool = True, particle_mass=None, out=None,
                     precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
                     accumulate: bool = False, mass_fixup: bool = True, cube_ids=None, stats: bool = False,
-                    workspace=None, stream=None, tuning=None):
+                    workspace=None, stream=None, tuning=None, cost_model=None):
     """pse_deposit_uniform: cell masses float64 [g2, g1, g0] (x fastest)."""
     torch = _torch()
     L = _lib.load()
@@ -103,7 +110,7 @@ def deposit_uniform(pos, n, grid_n, *, box: float = 1.0, periodic: bool = True, 
     g3, g = _grid3(grid_n)
     if out is None:
         out = torch.empty((g[2], g[1], g[0]), dtype=torch.float64, device=pos.device)
-    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, cube_ids, tuning)
+    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, cube_ids, tuning, cost_model)
     st = _lib.DepositStats() if stats else None
     ws_ptr, ws_bytes = (ctypes.c_void_p(None), 0) if workspace is None else \
         (_dev_ptr(workspace, torch.uint8, "workspace"), workspace.numel())
@@ -116,14 +123,15 @@ def deposit_uniform(pos, n, grid_n, *, box: float = 1.0, periodic: bool = True, 
 
 def deposit_tets(verts, tet_mass, grid_n, *, box: float = 1.0, periodic: bool = True, out=None,
                  precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0,
-                 accumulate: bool = False, mass_fixup: bool = True, stats: bool = False, workspace=None, stream=None):
+                 accumulate: bool = False, mass_fixup: bool = True, stats: bool = False, workspace=None, stream=None,
+                 tuning=None):
     """pse_deposit_tets: explicit tetrahedra verts float32 [T, 4, 3] (box units), masses float64 [T]."""
     torch = _torch()
     L = _lib.load()
     g3, g = _grid3(grid_n)
     if out is None:
         out = torch.empty((g[2], g[1], g[0]), dtype=torch.float64, device=verts.device)
-    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup)
+    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, tuning=tuning)
     st = _lib.DepositStats() if stats else None
     ws_ptr, ws_bytes = (ctypes.c_void_p(None), 0) if workspace is None else \
         (_dev_ptr(workspace, torch.uint8, "workspace"), workspace.numel())
@@ -155,8 +163,18 @@ def build_tets_from_lagrangian_grid(pos, n, *, box: float = 1.0, periodic: bool 
     return vidx, vol
 
 
-def workspace_size(op: int = _lib.PSE_OP_DEPOSIT_UNIFORM, lat=None) -> int:
-    return int(_lib.load().pse_workspace_size(op, ctypes.byref(lat) if lat is not None else None, None))
+def workspace_size(op: int = _lib.PSE_OP_DEPOSIT_UNIFORM, lat=None, schedule=None, cost_model=None) -> int:
+    """pse_workspace_size; schedule / cost_model: what the deposit will use (the binned schedule
+    needs room for its queue, and with a cost model for one bit per tetrahedron of lat)."""
+    o = None
+    if schedule is not None:
+        o = _lib.DepositOpts()
+        o.precision = PSE_FP32_FP64ACC
+        o.schedule = schedule
+        if cost_model is not None:
+            o.cost_model = cost_model.ptr
+    return int(_lib.load().pse_workspace_size(op, ctypes.byref(lat) if lat is not None else None,
+                                              ctypes.cast(ctypes.pointer(o), ctypes.c_void_p) if o is not None else None))
 
 
 def last_error() -> str:

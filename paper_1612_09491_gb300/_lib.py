@@ -32,6 +32,10 @@ PSE_OP_DEPOSIT_UNIFORM = 1
 PSE_OP_DEPOSIT_OCTREE = 2
 PSE_OP_BUILD_OCTREE = 3
 PSE_OP_DEPOSIT_TETS = 4
+PSE_COSTMODEL_NFEAT = 16
+PSE_COSTMODEL_NPARAMS = 5410
+PSE_TRAIN_FP32 = 1
+PSE_TRAIN_GRAD_ONLY = 2
 
 # every symbol include/pse.h declares (checked by the tests)
 EXPORTED = (
@@ -43,6 +47,13 @@ EXPORTED = (
     "pse_deposit_octree",
     "pse_free_octree",
     "pse_build_octree_leaves_noalloc",
+    "pse_costmodel_bytes",
+    "pse_costmodel_set",
+    "pse_costmodel_get",
+    "pse_costmodel_features",
+    "pse_tet_counts",
+    "pse_costmodel_predict",
+    "pse_costmodel_train_step",
     "pse_workspace_size",
     "pse_last_error",
     "pse_abi_version",
@@ -81,7 +92,8 @@ class Octree(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("bin_edges", ctypes.c_int32 * 7), ("reserved", ctypes.c_int32)]
+                ("split_cells", ctypes.c_int32), ("chunk_cells", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 class PseError(RuntimeError):
@@ -129,6 +141,21 @@ def load(build_if_missing: bool = False):
         L.pse_build_octree_leaves_noalloc.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int32, ctypes.c_int32,
                                                       ctypes.c_double, vp, ctypes.c_int64, vp, vp]
         L.pse_build_octree_leaves_noalloc.restype = ctypes.c_int
+        L.pse_costmodel_bytes.argtypes = []
+        L.pse_costmodel_bytes.restype = ctypes.c_size_t
+        L.pse_costmodel_set.argtypes = [vp, vp, vp]
+        L.pse_costmodel_set.restype = ctypes.c_int
+        L.pse_costmodel_get.argtypes = [vp, vp, vp, vp]
+        L.pse_costmodel_get.restype = ctypes.c_int
+        L.pse_costmodel_features.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.POINTER(ctypes.c_int64), vp, vp]
+        L.pse_costmodel_features.restype = ctypes.c_int
+        L.pse_tet_counts.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.POINTER(ctypes.c_int64), ctypes.c_double,
+                                     vp, vp]
+        L.pse_tet_counts.restype = ctypes.c_int
+        L.pse_costmodel_predict.argtypes = [vp, vp, ctypes.c_int64, vp, vp]
+        L.pse_costmodel_predict.restype = ctypes.c_int
+        L.pse_costmodel_train_step.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, vp, vp]
+        L.pse_costmodel_train_step.restype = ctypes.c_int
         L.pse_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(Lattice), vp]
         L.pse_workspace_size.restype = ctypes.c_size_t
         L.pse_last_error.argtypes = []

@@ -11,6 +11,12 @@ import json
 import os
 
 CANDIDATES = ({"blocks_per_sm": 1}, {"blocks_per_sm": 2})
+# uniform-grid deposits: the warp-cooperative kernel, and the binned persistent schedule
+# over its split threshold, split work-item size and residency (launched as a CUDA graph)
+UNIFORM_CANDIDATES = tuple([{"schedule": "warp", "blocks_per_sm": b} for b in (1, 2)] +
+                           [{"schedule": "binned", "blocks_per_sm": b, "split_cells": sp, "chunk_cells": ch,
+                             "use_graph": 1}
+                            for b in (1, 2) for sp in (256, 1024, 4096) for ch in (256, 1024)])
 _mem = {}
 
 

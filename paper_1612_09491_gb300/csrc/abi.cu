@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -72,25 +73,51 @@ struct WsLease {
     }
 };
 
-int acquire_ws(void *d_ws, size_t ws_bytes, cudaStream_t st, WsLease &lease)
+// need: total bytes (the Workspace header is cleared; anything after it is scratch)
+int acquire_ws(void *d_ws, size_t ws_bytes, cudaStream_t st, WsLease &lease, size_t need = pse::kWorkspaceBytes,
+               bool clear = true)
 {
     lease.st = st;
     if (d_ws == nullptr) {
         if (ws_bytes != 0) return fail(PSE_ERR_INVALID_ARG, "d_ws is NULL but ws_bytes is %zu", ws_bytes);
         void *p = nullptr;
-        cudaError_t e = cudaMallocAsync(&p, pse::kWorkspaceBytes, st);
+        cudaError_t e = cudaMallocAsync(&p, need, st);
         if (e != cudaSuccess) return fail(PSE_ERR_OOM, "workspace allocation failed: %s", cudaGetErrorString(e));
         lease.ws = static_cast<pse::Workspace *>(p);
         lease.owned = true;
     } else {
-        if (ws_bytes < pse::kWorkspaceBytes)
-            return fail(PSE_ERR_WORKSPACE, "ws_bytes = %zu < required %zu", ws_bytes, pse::kWorkspaceBytes);
+        if (ws_bytes < need)
+            return fail(PSE_ERR_WORKSPACE, "ws_bytes = %zu < required %zu", ws_bytes, need);
         if (reinterpret_cast<uintptr_t>(d_ws) % 16 != 0) return fail(PSE_ERR_INVALID_ARG, "d_ws must be 16-byte aligned");
         lease.ws = static_cast<pse::Workspace *>(d_ws);
     }
+    if (!clear) return PSE_OK;
     cudaError_t e = cudaMemsetAsync(lease.ws, 0, pse::kWorkspaceBytes, st);
     if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
     return PSE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of the binned deposit: the call's launch sequence (workspace and output
+// clears, bin pass, scan, persistent kernel, renormalisation) is captured once per
+// distinct argument set and replayed afterwards.
+// ---------------------------------------------------------------------------
+struct GraphEntry {
+    std::string key;
+    int dev;
+    cudaGraphExec_t exec;
+};
+std::mutex g_graph_mu;
+std::vector<GraphEntry> g_graphs;       // most recently used last
+constexpr size_t kMaxGraphs = 16;
+cudaStream_t g_capture_stream[64] = {};
+
+std::string graph_key(const pse::DepositParams &p, int64_t cells, bool accumulate, bool renorm, int bps)
+{
+    std::string k(reinterpret_cast<const char *>(&p), sizeof(p));
+    const int64_t extra[4] = {cells, accumulate ? 1 : 0, renorm ? 1 : 0, bps};
+    k.append(reinterpret_cast<const char *>(extra), sizeof(extra));
+    return k;
 }
 
 int check_grid(const int64_t grid_n[3], int64_t &cells)
@@ -111,9 +138,8 @@ int check_opts(const pse_deposit_opts &o)
         return fail(PSE_ERR_INVALID_ARG, "unknown precision %d", o.precision);
     if (o.schedule != PSE_THREAD_PER_TET && o.schedule != PSE_WARP_COOPERATIVE && o.schedule != PSE_BINNED_PERSISTENT)
         return fail(PSE_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
-    if (o.schedule == PSE_BINNED_PERSISTENT) return fail(PSE_ERR_UNSUPPORTED, "PSE_BINNED_PERSISTENT is not available");
-    if (o.schedule == PSE_WARP_COOPERATIVE && o.precision != PSE_FP32_FP64ACC)
-        return fail(PSE_ERR_UNSUPPORTED, "the warp-cooperative schedule runs the FP32 clip (precision 1)");
+    if (o.schedule != PSE_THREAD_PER_TET && o.precision != PSE_FP32_FP64ACC)
+        return fail(PSE_ERR_UNSUPPORTED, "the warp-cooperative and binned schedules run the FP32 clip (precision 1)");
     if (o.n_cube_ids < 0) return fail(PSE_ERR_INVALID_ARG, "n_cube_ids < 0");
     if (o.n_cube_ids > 0 && !o.d_cube_ids) return fail(PSE_ERR_INVALID_ARG, "n_cube_ids > 0 but d_cube_ids is NULL");
     return PSE_OK;
@@ -128,45 +154,132 @@ void fill_grid(pse::DepositParams &p, const int64_t grid_n[3], double box)
     }
 }
 
+constexpr int kDefaultSplitCells = 1024;
+constexpr int kDefaultChunkCells = 512;
+
+// workspace of a deposit; n_tets < 0: unknown (0 is returned if it matters)
+size_t deposit_ws_bytes(const pse_deposit_opts *o, int64_t n_tets)
+{
+    if (!o || o->schedule != PSE_BINNED_PERSISTENT) return pse::kWorkspaceBytes;
+    if (!o->cost_model) return pse::kWorkspaceBytes + pse::kQueueBytes;
+    if (n_tets < 0) return 0;
+    return pse::kWorkspaceBytes + pse::kQueueBytes + pse::qbits_bytes(n_tets);
+}
+
 int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells, pse_deposit_stats *h_stats,
                 void *d_ws, size_t ws_bytes, cudaStream_t st)
 {
+    const bool binned = o.schedule == PSE_BINNED_PERSISTENT && !p.leaves;
+    const pse_tuning *tu = static_cast<const pse_tuning *>(o.tuning);
+    const bool stats = h_stats != nullptr;
+    const bool graph = binned && tu && tu->use_graph && d_ws != nullptr && !stats;
     WsLease lease;
-    int rc = acquire_ws(d_ws, ws_bytes, st, lease);
+    const int64_t n_tets = (p.src == pse::SRC_TETS) ? p.n_units : 6 * p.n_units;
+    int rc = acquire_ws(d_ws, ws_bytes, st, lease, deposit_ws_bytes(&o, n_tets), false);
     if (rc != PSE_OK) return rc;
     p.ws = lease.ws;
+    size_t qbits_len = 0;
+    if (binned && o.cost_model) {
+        p.model = static_cast<const pse::CostModelDev *>(o.cost_model);
+        p.qbits = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes +
+                                               pse::kQueueBytes);
+        qbits_len = pse::qbits_bytes(n_tets);
+    }
+    if (binned) {
+        unsigned char *q = reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes;
+        p.q_tet = reinterpret_cast<int64_t *>(q);
+        p.chunk_start = reinterpret_cast<int64_t *>(q + (size_t)pse::kQueueCap * 8);
+        p.q_cells = reinterpret_cast<int32_t *>(q + (size_t)pse::kQueueCap * 8 + (size_t)(pse::kQueueCap + 1) * 8);
+        p.q_cap = pse::kQueueCap;
+        p.split_cells = (tu && tu->split_cells > 0) ? tu->split_cells : kDefaultSplitCells;
+        p.chunk_cells = (tu && tu->chunk_cells > 0) ? tu->chunk_cells : kDefaultChunkCells;
+        if (p.chunk_cells > (1 << 24)) p.chunk_cells = 1 << 24;
+    }
     p.kappa_max = kappa_limit(o.guard_eps);
     // FP32 mass renormalisation: the call's deposits are scaled by sum(m_t)/sum(deposits);
     // it needs the output to hold this call's deposits only (accumulate = 0)
     const bool renorm = o.mass_fixup && !o.accumulate && o.precision == PSE_FP32_FP64ACC;
     p.fixup = renorm ? 1 : 0;
-    cudaError_t e;
-    if (!o.accumulate) {
-        e = cudaMemsetAsync(p.out, 0, (size_t)cells * sizeof(double), st);
-        if (e != cudaSuccess) return cuda_fail(e, "output clear");
-    }
-    const bool stats = h_stats != nullptr;
-    if (p.n_units > 0 && p.leaves) {
-        const pse_tuning *tu = static_cast<const pse_tuning *>(o.tuning);
-        const int bps = (tu && tu->blocks_per_sm > 0) ? tu->blocks_per_sm : kDefaultBlocksPerSm;
-        if (o.schedule != PSE_THREAD_PER_TET)
-            p.n_items = (p.src == pse::SRC_LATTICE) ? ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2] : (p.n_units + 31) / 32;
-        e = pse::launch_octree_deposit(p, o.precision == PSE_FP64_PLAIN, o.schedule == PSE_THREAD_PER_TET, stats, bps, st);
-        if (e != cudaSuccess) return cuda_fail(e, "octree deposit launch");
-    } else if (p.n_units > 0) {
-        if (o.schedule == PSE_THREAD_PER_TET) {
-            e = pse::launch_thread_per_tet(p, o.precision == PSE_FP64_PLAIN, stats, st);
-        } else {
-            p.n_items = (p.src == pse::SRC_LATTICE) ? ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2] : (p.n_units + 31) / 32;
-            const pse_tuning *tu = static_cast<const pse_tuning *>(o.tuning);
-            const int bps = (tu && tu->blocks_per_sm > 0) ? tu->blocks_per_sm : kDefaultBlocksPerSm;
-            e = pse::launch_warp_coop(p, stats, bps, st);
+    const int bps = (tu && tu->blocks_per_sm > 0) ? tu->blocks_per_sm : kDefaultBlocksPerSm;
+    if (p.n_units > 0 && o.schedule != PSE_THREAD_PER_TET)
+        p.n_items = (p.src == pse::SRC_LATTICE) ? ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2] : (p.n_units + 31) / 32;
+
+    // the whole launch sequence of the call, on stream s
+    auto enqueue = [&](cudaStream_t s) -> int {
+        cudaError_t e = cudaMemsetAsync(p.ws, 0, pse::kWorkspaceBytes, s);
+        if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
+        if (qbits_len) {
+            e = cudaMemsetAsync(p.qbits, 0, qbits_len, s);
+            if (e != cudaSuccess) return cuda_fail(e, "queue bitmap clear");
         }
-        if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
-    }
-    if (renorm && p.n_units > 0) {
-        e = pse::launch_scale(p.out, cells, p.ws, st);
-        if (e != cudaSuccess) return cuda_fail(e, "mass renormalisation launch");
+        if (!o.accumulate) {
+            e = cudaMemsetAsync(p.out, 0, (size_t)cells * sizeof(double), s);
+            if (e != cudaSuccess) return cuda_fail(e, "output clear");
+        }
+        if (p.n_units > 0 && p.leaves) {
+            e = pse::launch_octree_deposit(p, o.precision == PSE_FP64_PLAIN, o.schedule == PSE_THREAD_PER_TET, stats,
+                                           bps, s);
+            if (e != cudaSuccess) return cuda_fail(e, "octree deposit launch");
+        } else if (p.n_units > 0) {
+            if (o.schedule == PSE_THREAD_PER_TET) e = pse::launch_thread_per_tet(p, o.precision == PSE_FP64_PLAIN, stats, s);
+            else if (binned) e = pse::launch_binned(p, stats, bps, s);
+            else e = pse::launch_warp_coop(p, stats, bps, s);
+            if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+        }
+        if (renorm && p.n_units > 0) {
+            e = pse::launch_scale(p.out, cells, p.ws, s);
+            if (e != cudaSuccess) return cuda_fail(e, "mass renormalisation launch");
+        }
+        return PSE_OK;
+    };
+
+    cudaError_t e;
+    if (!graph) {
+        rc = enqueue(st);
+        if (rc != PSE_OK) return rc;
+    } else {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        if (dev < 0 || dev >= 64) return fail(PSE_ERR_UNSUPPORTED, "device index beyond the supported range");
+        const std::string key = graph_key(p, cells, o.accumulate != 0, renorm, bps);
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        cudaGraphExec_t exec = nullptr;
+        for (size_t i = 0; i < g_graphs.size(); ++i)
+            if (g_graphs[i].dev == dev && g_graphs[i].key == key) {
+                GraphEntry hit = g_graphs[i];
+                g_graphs.erase(g_graphs.begin() + (long)i);
+                g_graphs.push_back(hit);
+                exec = hit.exec;
+                break;
+            }
+        if (!exec) {
+            if (!g_capture_stream[dev]) {
+                e = cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking);
+                if (e != cudaSuccess) return cuda_fail(e, "capture stream");
+            }
+            cudaStream_t cs = g_capture_stream[dev];
+            e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(e, "graph capture begin");
+            const int rc2 = enqueue(cs);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(cs, &g);
+            if (rc2 != PSE_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc2;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
+            e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+            if (g_graphs.size() >= kMaxGraphs) {
+                cudaGraphExecDestroy(g_graphs.front().exec);
+                g_graphs.erase(g_graphs.begin());
+            }
+            g_graphs.push_back(GraphEntry{key, dev, exec});
+        }
+        e = cudaGraphLaunch(exec, st);
+        if (e != cudaSuccess) return cuda_fail(e, "graph launch");
     }
     if (stats) {
         pse::Workspace hw;
@@ -340,11 +453,14 @@ int pse_abi_version(void) { return PSE_ABI_VERSION; }
 
 size_t pse_workspace_size(int op, const pse_lattice *lat, const void *op_params)
 {
-    (void)lat;
-    (void)op_params;
     switch (op) {
     case PSE_OP_DEPOSIT_UNIFORM:
+        return deposit_ws_bytes(static_cast<const pse_deposit_opts *>(op_params),
+                                lat ? 6 * (lat->periodic ? lat->n[0] * lat->n[1] * lat->n[2]
+                                                         : (lat->n[0] - 1) * (lat->n[1] - 1) * (lat->n[2] - 1))
+                                    : -1);
     case PSE_OP_DEPOSIT_TETS:
+        return deposit_ws_bytes(static_cast<const pse_deposit_opts *>(op_params), -1);
     case PSE_OP_DEPOSIT_OCTREE:
         return pse::kWorkspaceBytes;
     case PSE_OP_BUILD_OCTREE: {
@@ -545,6 +661,110 @@ int pse_deposit_tets(const float *d_verts, const double *d_tet_mass, int64_t n_t
     fill_grid(p, grid_n, box);
     p.out = d_cell_mass;
     return run_deposit(p, o, cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// cost model
+// ---------------------------------------------------------------------------
+size_t pse_costmodel_bytes(void) { return pse::costmodel_bytes(); }
+
+int pse_costmodel_set(void *d_model, const float *h_params, void *stream)
+{
+    g_last_error.clear();
+    if (!d_model || !h_params) return fail(PSE_ERR_INVALID_ARG, "d_model and h_params must be non-NULL");
+    if (reinterpret_cast<uintptr_t>(d_model) % 16 != 0) return fail(PSE_ERR_INVALID_ARG, "d_model must be 16-byte aligned");
+    for (int i = 16; i < 32; ++i)
+        if (!(h_params[i] > 0.0f) || !std::isfinite(h_params[i]))
+            return fail(PSE_ERR_INVALID_ARG, "feature scale %d must be finite and > 0", i - 16);
+    cudaError_t e = pse::costmodel_set(static_cast<pse::CostModelDev *>(d_model), h_params,
+                                       static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSE_OK : cuda_fail(e, "cost model upload");
+}
+
+int pse_costmodel_get(const void *d_model, float *h_params, float *h_grad, void *stream)
+{
+    g_last_error.clear();
+    if (!d_model) return fail(PSE_ERR_INVALID_ARG, "d_model is NULL");
+    cudaError_t e = pse::costmodel_get(static_cast<const pse::CostModelDev *>(d_model), h_params, h_grad,
+                                       static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSE_OK : cuda_fail(e, "cost model download");
+}
+
+namespace {
+int lattice_grid_params(const float *d_pos, const pse_lattice *lat, const int64_t grid_n[3], pse::DepositParams &p)
+{
+    if (!d_pos) return fail(PSE_ERR_INVALID_ARG, "d_pos is NULL");
+    int rc = check_lattice(lat);
+    if (rc != PSE_OK) return rc;
+    int64_t cells = 0;
+    rc = check_grid(grid_n, cells);
+    if (rc != PSE_OK) return rc;
+    std::memset(&p, 0, sizeof(p));
+    p.periodic = lat->periodic ? 1 : 0;
+    p.pos = d_pos;
+    for (int a = 0; a < 3; ++a) {
+        p.n[a] = lat->n[a];
+        p.nc[a] = p.periodic ? lat->n[a] : lat->n[a] - 1;
+    }
+    p.box = lat->box;
+    p.m_tet = lat->particle_mass / 6.0;
+    fill_grid(p, grid_n, lat->box);
+    p.src = pse::SRC_LATTICE;
+    p.n_units = p.nc[0] * p.nc[1] * p.nc[2];
+    return PSE_OK;
+}
+}  // namespace
+
+int pse_costmodel_features(const float *d_pos, const pse_lattice *lat, const int64_t grid_n[3], float *d_feat,
+                           void *stream)
+{
+    g_last_error.clear();
+    pse::DepositParams p;
+    int rc = lattice_grid_params(d_pos, lat, grid_n, p);
+    if (rc != PSE_OK) return rc;
+    if (!d_feat) return fail(PSE_ERR_INVALID_ARG, "d_feat is NULL");
+    if (p.n_units == 0) return PSE_OK;
+    cudaError_t e = pse::launch_features(p, d_feat, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSE_OK : cuda_fail(e, "features launch");
+}
+
+int pse_tet_counts(const float *d_pos, const pse_lattice *lat, const int64_t grid_n[3], double guard_eps,
+                   int32_t *d_counts, void *stream)
+{
+    g_last_error.clear();
+    pse::DepositParams p;
+    int rc = lattice_grid_params(d_pos, lat, grid_n, p);
+    if (rc != PSE_OK) return rc;
+    if (!d_counts) return fail(PSE_ERR_INVALID_ARG, "d_counts is NULL");
+    p.kappa_max = kappa_limit(guard_eps);
+    if (p.n_units == 0) return PSE_OK;
+    cudaError_t e = pse::launch_tet_counts(p, d_counts, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSE_OK : cuda_fail(e, "counts launch");
+}
+
+int pse_costmodel_predict(const void *d_model, const float *d_feat, int64_t n, float *d_out, void *stream)
+{
+    g_last_error.clear();
+    if (!d_model || (n > 0 && (!d_feat || !d_out)) || n < 0)
+        return fail(PSE_ERR_INVALID_ARG, "d_model, d_feat and d_out must be non-NULL and n >= 0");
+    if (n == 0) return PSE_OK;
+    cudaError_t e = pse::launch_predict(static_cast<const pse::CostModelDev *>(d_model), d_feat, n, d_out,
+                                        static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSE_OK : cuda_fail(e, "predict launch");
+}
+
+int pse_costmodel_train_step(void *d_model, const float *d_feat, const float *d_target, const int64_t *d_index,
+                             int64_t batch, float lr, int32_t flags, double *d_loss, void *stream)
+{
+    g_last_error.clear();
+    if (!d_model || !d_feat || !d_target || !d_loss || batch < 1)
+        return fail(PSE_ERR_INVALID_ARG, "d_model, d_feat, d_target and d_loss must be non-NULL and batch >= 1");
+    if (!(lr >= 0.0f) || !std::isfinite(lr)) return fail(PSE_ERR_INVALID_ARG, "lr must be finite and >= 0");
+    if (flags & ~(PSE_TRAIN_FP32 | PSE_TRAIN_GRAD_ONLY)) return fail(PSE_ERR_INVALID_ARG, "unknown flags %d", flags);
+    cudaError_t e = pse::launch_train_step(static_cast<pse::CostModelDev *>(d_model), d_feat, d_target, d_index, batch, lr,
+                                           (flags & PSE_TRAIN_FP32) != 0, (flags & PSE_TRAIN_GRAD_ONLY) == 0, d_loss,
+                                           static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSE_OK : cuda_fail(e, "training step launch");
 }
 
 }  // extern "C"

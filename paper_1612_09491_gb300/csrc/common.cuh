@@ -288,6 +288,7 @@ struct WarpSmem {
     int org[3][32];       // octree: the leaf's first cell, base-cell frame
     double rho[32];
     int start[32];        // exclusive prefix of the pair counts
+    int skip[32];         // first bounding-box cell of this record (split tetrahedra; else 0)
     int guard[32];        // 1: clip this tetrahedron in float64
     float vlo[12][32];    // guarded tetrahedra: rounding residuals of v (exact = v + vlo)
     unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
@@ -336,6 +337,38 @@ __device__ __forceinline__ void store_residuals(WarpSmem *S, int lane, const P3<
         S->vlo[3 * q + 1][lane] = r[q].y;
         S->vlo[3 * q + 2][lane] = r[q].z;
     }
+}
+
+// Record lane's tetrahedron (uniform grid) for the pair machinery.
+__device__ __forceinline__ void store_record(WarpSmem *S, int lane, const TetSetup<float> &ts,
+                                             const P3<float> (&res)[4], const int (&base)[3], double m_t,
+                                             float kappa_max, int skip)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        S->v[3 * q][lane] = ts.v[q].x;
+        S->v[3 * q + 1][lane] = ts.v[q].y;
+        S->v[3 * q + 2][lane] = ts.v[q].z;
+        S->n[3 * q][lane] = ts.n[q].x;
+        S->n[3 * q + 1][lane] = ts.n[q].y;
+        S->n[3 * q + 2][lane] = ts.n[q].z;
+        S->e[q][lane] = ts.e[q];
+        S->pos[q][lane] = ts.pos[q];
+        S->neg[q][lane] = ts.neg[q];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        S->lo[a][lane] = ts.lo[a];
+        S->dim[a][lane] = ts.dim[a];
+        S->base[a][lane] = base[a];
+    }
+    const int guard = (ts.kappa <= kappa_max) ? 0 : 1;
+    S->rho[lane] = 6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6);
+    S->lx[lane] = ts.lx;
+    S->ly[lane] = ts.ly;
+    S->guard[lane] = guard;
+    S->skip[lane] = skip;
+    if (guard) store_residuals(S, lane, res);
 }
 
 // Add m to cell (cx, cy, cz) (base-cell frame) of virtual tetrahedron t: the uniform
@@ -406,54 +439,59 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
     const int total = __shfl_sync(kFull, incl, 31);
     S->start[lane] = incl - npairs;
     __syncwarp();
+    // one clip_round call site, so that the clip is inlined once (instruction-cache footprint)
     int qn = 0;
-    for (int b0 = 0; b0 < total; b0 += 32) {
-        const int idx = b0 + lane;
-        bool partial = false;
-        unsigned long long ent = 0;
-        if (idx < total) {
-            int t = 0;
+    for (int b0 = 0;; b0 += 32) {
+        if (b0 < total) {
+            const int idx = b0 + lane;
+            bool partial = false;
+            unsigned long long ent = 0;
+            if (idx < total) {
+                int t = 0;
 #pragma unroll
-            for (int step = 16; step >= 1; step >>= 1)
-                if (S->start[t + step] <= idx && t + step < 32) t += step;
-            const int local = idx - S->start[t];
-            int ix, iy, iz;
-            decompose(local, S->dim[0][t], S->dim[1][t], ix, iy, iz);
-            const float cx = (float)(S->lo[0][t] + ix), cy = (float)(S->lo[1][t] + iy),
-                        cz = (float)(S->lo[2][t] + iz);
-            P3<float> n[4];
-            float e[4], ps[4], ng[4];
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (S->start[t + step] <= idx && t + step < 32) t += step;
+                const int local = idx - S->start[t] + S->skip[t];
+                int ix, iy, iz;
+                decompose(local, S->dim[0][t], S->dim[1][t], ix, iy, iz);
+                const float cx = (float)(S->lo[0][t] + ix), cy = (float)(S->lo[1][t] + iy),
+                            cz = (float)(S->lo[2][t] + iz);
+                P3<float> n[4];
+                float e[4], ps[4], ng[4];
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
-                e[f] = S->e[f][t];
-                ps[f] = S->pos[f][t];
-                ng[f] = S->neg[f][t];
+                for (int f = 0; f < 4; ++f) {
+                    n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
+                    e[f] = S->e[f][t];
+                    ps[f] = S->pos[f][t];
+                    ng[f] = S->neg[f][t];
+                }
+                const int cls = classify_cell<float>(n, e, ps, ng, cx, cy, cz);
+                if (cls == CELL_INSIDE) {
+                    const double m = S->rho[t];
+                    cnt.dep += m;
+                    if (!deposit_pair<OCT>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) && STATS)
+                        cnt.dropped += m;
+                    if (STATS) cnt.u[ST_INSIDE_CELLS]++;
+                } else if (cls == CELL_PARTIAL) {
+                    partial = true;
+                    ent = q_pack(t, ix, iy, iz);
+                }
             }
-            const int cls = classify_cell<float>(n, e, ps, ng, cx, cy, cz);
-            if (cls == CELL_INSIDE) {
-                const double m = S->rho[t];
-                cnt.dep += m;
-                if (!deposit_pair<OCT>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) && STATS)
-                    cnt.dropped += m;
-                if (STATS) cnt.u[ST_INSIDE_CELLS]++;
-            } else if (cls == CELL_PARTIAL) {
-                partial = true;
-                ent = q_pack(t, ix, iy, iz);
-            }
-        }
-        const unsigned bal = __ballot_sync(kFull, partial);
-        if (partial) S->q[qn + __popc(bal & lt_mask)] = ent;
-        qn += __popc(bal);
-        __syncwarp();
-        if (qn >= 32) {
-            clip_round<STATS, OCT>(P, S, 32, lane, cnt);
-            if (lane < qn - 32) S->q[lane] = S->q[32 + lane];
-            qn -= 32;
+            const unsigned bal = __ballot_sync(kFull, partial);
+            if (partial) S->q[qn + __popc(bal & lt_mask)] = ent;
+            qn += __popc(bal);
             __syncwarp();
         }
+        const bool last = b0 + 32 >= total;
+        if (qn >= 32 || (last && qn > 0)) {
+            const int take = qn >= 32 ? 32 : qn;
+            clip_round<STATS, OCT>(P, S, take, lane, cnt);
+            if (lane < qn - take) S->q[lane] = S->q[take + lane];
+            qn -= take;
+            __syncwarp();
+        }
+        if (last && qn == 0) break;
     }
-    if (qn > 0) clip_round<STATS, OCT>(P, S, qn, lane, cnt);
 }
 
 

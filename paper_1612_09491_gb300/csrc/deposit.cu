@@ -15,6 +15,7 @@
 //    rounding residual m_t - sum can be added to the cell of its centroid.
 //  * k_build_tets: particle indices and signed volumes of every tetrahedron.
 #include "common.cuh"
+#include "costmodel.cuh"
 
 namespace pse {
 
@@ -124,7 +125,45 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
 // ---------------------------------------------------------------------------
 // warp-cooperative FP32 path
 // ---------------------------------------------------------------------------
-template <bool STATS, int MINB>
+// Split work item `item` of the binned schedule: chunk [first, first + len) of the
+// bounding-box cells of one queued tetrahedron, set up by lane 0 as record 0.  Returns
+// the lane's pair count (len on lane 0, else 0).
+template <bool STATS>
+__device__ __forceinline__ int chunk_setup(const DepositParams &P, WarpSmem *S, int lane, int64_t item, int64_t q,
+                                           Counters &cnt)
+{
+    // queue entry e: the last with chunk_start[e] <= item
+    int64_t lo = 0, hi = q - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (P.chunk_start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t first = (item - P.chunk_start[lo]) * (int64_t)P.chunk_cells;
+    const int64_t ncell = P.q_cells[lo];
+    const int len = (int)min((int64_t)P.chunk_cells, ncell - first);
+    if (lane != 0 || len <= 0) return 0;
+    const int64_t id = P.q_tet[lo];
+    P3<float> v[4], res[4];
+    int base[3];
+    double m_t;
+    if (P.src == SRC_TETS) {
+        explicit_tet<float>(P, id, v, base, res);
+        m_t = P.tet_mass[id];
+    } else {
+        int64_t ci, cj, ck;
+        if (!cube_of_unit(P, id / 6, ci, cj, ck)) return 0;
+        lattice_tet<float>(P, ci, cj, ck, (int)(id % 6), v, base, res);
+        m_t = P.m_tet;
+    }
+    TetSetup<float> ts;
+    if (tet_setup<float>(v, ts)) swap12(res);
+    store_record(S, 0, ts, res, base, m_t, P.kappa_max, (int)first);
+    if (STATS) cnt.u[ST_BBOX_CELLS] += len;
+    return len;
+}
+
+template <bool STATS, int MINB, bool BINNED>
 __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -134,17 +173,32 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
     if (STATS) cnt.zero();
     cnt.zero_mass();
     const int nsub = (P.src == SRC_TETS) ? 1 : 6;
+    // binned schedule: items [0, n_chunks) are pieces of split tetrahedra (largest work
+    // first), the rest are the rows; tetrahedra the bin pass queued are skipped there
+    int64_t n_chunks = 0, q = 0;
+    bool split = false;
+    if (BINNED) {
+        split = P.ws->queue_overflow == 0;
+        n_chunks = split ? (int64_t)P.ws->n_chunk_items : 0;
+        q = split ? min((int64_t)P.ws->queue_count, P.q_cap) : 0;
+    }
 
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(&P.ws->work_counter, 1ull);
         item = __shfl_sync(kFull, item, 0);
-        if ((int64_t)item >= P.n_items) break;
+        const bool is_chunk = BINNED && (int64_t)item < n_chunks;
+        if (!is_chunk) {
+            item -= (unsigned long long)n_chunks;
+            if ((int64_t)item >= P.n_items) break;
+        }
 
         // the 32 units (cubes or tetrahedra) of this item
         int64_t unit = -1;
         int64_t ci = 0, cj = 0, ck = 0;
-        if (P.src == SRC_LATTICE) {
+        if (is_chunk) {
+            // nothing: chunk_setup below
+        } else if (P.src == SRC_LATTICE) {
             // rows of 32 cubes along x
             const int64_t segs = (P.nc[0] + 31) / 32;
             const int64_t row = (int64_t)item / segs, seg = (int64_t)item % segs;
@@ -166,13 +220,20 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
             }
         }
 
-        for (int s = 0; s < nsub; ++s) {
-            // ---- 1. one tetrahedron per lane
+        const int nsub_item = is_chunk ? 1 : nsub;
+        for (int s = 0; s < nsub_item; ++s) {
+            // ---- 1. one tetrahedron per lane (or the queued tetrahedron's chunk on lane 0)
             int npairs = 0;
             double m_t = 0.0;
-            if (unit >= 0) {
+            if (is_chunk) {
+                npairs = chunk_setup<STATS>(P, S, lane, (int64_t)item, q, cnt);
+                __syncwarp();
+            } else if (unit >= 0) {
                 P3<float> v[4], res[4];
                 int base[3];
+                // tetrahedron id as the bin pass numbers it
+                const int64_t tid = (P.src == SRC_TETS) ? unit
+                                    : 6 * ((P.src == SRC_LATTICE) ? ci + P.nc[0] * (cj + P.nc[1] * ck) : unit) + s;
                 if (P.src == SRC_TETS) {
                     explicit_tet<float>(P, unit, v, base, res);
                     m_t = P.tet_mass[unit];
@@ -202,36 +263,19 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
                     cnt.tgt += m_t;
                     cnt.dep += m_t;
                     if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
+                } else if (BINNED && split &&
+                           (P.model ? ((P.qbits[tid >> 5] >> (tid & 31)) & 1u) != 0
+                                    : (ncell > P.split_cells && ncell <= (int64_t)INT32_MAX))) {
+                    // queued by the bin pass: its cells are done by the split work items
+                    cnt.tgt += m_t;
+                    if (STATS) cnt.u[ST_BIN0 + size_bin(ncell)]++;
                 } else if (ncell > (int64_t)(1 << 25)) {
                     set_error(P.ws, 2, lane);  // 32 x 2^25 pairs still fit the int32 scan
                 } else {
                     npairs = (int)ncell;
                     cnt.tgt += m_t;
                     if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        S->v[3 * q][lane] = ts.v[q].x;
-                        S->v[3 * q + 1][lane] = ts.v[q].y;
-                        S->v[3 * q + 2][lane] = ts.v[q].z;
-                        S->n[3 * q][lane] = ts.n[q].x;
-                        S->n[3 * q + 1][lane] = ts.n[q].y;
-                        S->n[3 * q + 2][lane] = ts.n[q].z;
-                        S->e[q][lane] = ts.e[q];
-                        S->pos[q][lane] = ts.pos[q];
-                        S->neg[q][lane] = ts.neg[q];
-                    }
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) {
-                        S->lo[a][lane] = ts.lo[a];
-                        S->dim[a][lane] = ts.dim[a];
-                        S->base[a][lane] = base[a];
-                    }
-                    const int guard = (ts.kappa <= P.kappa_max) ? 0 : 1;
-                    S->rho[lane] = 6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6);
-                    S->lx[lane] = ts.lx;
-                    S->ly[lane] = ts.ly;
-                    S->guard[lane] = guard;
-                    if (guard) store_residuals(S, lane, res);
+                    store_record(S, lane, ts, res, base, m_t, P.kappa_max, 0);
                 }
             }
             // ---- 2. pair enumeration and clips
@@ -241,6 +285,114 @@ __global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
     }
     if (STATS) cnt.flush(P.ws);
     if (P.fixup) cnt.flush_mass(P.ws);
+}
+
+// ---------------------------------------------------------------------------
+// binned schedule: the bin pass queues every tetrahedron whose bounding box has more
+// than split_cells cells (warp-aggregated appends); the scan turns their cell counts
+// into work items of chunk_cells cells.
+// ---------------------------------------------------------------------------
+// Without a cost model a tetrahedron is queued when its bounding box has more than
+// split_cells cells (the row path recomputes the same test).  With one, the bin pass
+// predicts each tetrahedron's partial clips (warp MLP on the tensor cores), queues it
+// when the prediction exceeds split_cells, and marks it in the qbits bitmap that the row
+// path reads.
+template <bool MODEL>
+__global__ void __launch_bounds__(128) k_bin_pass(const DepositParams P)
+{
+    __shared__ MlpSmem msm[MODEL ? 4 : 1];
+    const int lane = threadIdx.x & 31;
+    const int64_t n_tets = (P.src == SRC_TETS) ? P.n_units : 6 * P.n_units;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together so that the ballot and the warp MLP see every lane
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n_tets; t0 += stride) {
+        const int64_t t = t0 + lane;
+        bool cand = false;
+        int64_t ncell = 0;
+        float f[kNFeat];
+        if (MODEL) {
+#pragma unroll
+            for (int q = 0; q < kNFeat; ++q) f[q] = 0.f;
+        }
+        if (t < n_tets) {
+            P3<float> v[4];
+            int base[3];
+            bool ok = true;
+            if (P.src == SRC_TETS) {
+                explicit_tet<float>(P, t, v, base);
+            } else {
+                int64_t ci, cj, ck;
+                ok = cube_of_unit(P, t / 6, ci, cj, ck);
+                if (ok) lattice_tet<float>(P, ci, cj, ck, (int)(t % 6), v, base);
+            }
+            if (ok) {
+                TetSetup<float> ts;
+                tet_setup<float>(v, ts);
+                ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
+                cand = tet_ok(base, ts) && ts.vol6 != 0.0 && ncell > 1 && ncell <= (int64_t)INT32_MAX;
+                if (MODEL && cand) tet_features(ts, f);
+            }
+        }
+        bool queue;
+        if (MODEL) {
+            float y[kNOut];
+            mlp_warp(P.model, msm[(threadIdx.x >> 5) & 3], lane, f, y);
+            queue = cand && expm1f(y[1]) > (float)P.split_cells;
+        } else {
+            queue = cand && ncell > P.split_cells;
+        }
+        const unsigned bal = __ballot_sync(kFull, queue);
+        if (bal) {
+            unsigned long long b0 = 0;
+            if (lane == 0) b0 = atomicAdd(&P.ws->queue_count, (unsigned long long)__popc(bal));
+            b0 = __shfl_sync(kFull, b0, 0);
+            if (queue) {
+                const int64_t idx = (int64_t)b0 + __popc(bal & ((1u << lane) - 1u));
+                if (idx < P.q_cap) {
+                    P.q_tet[idx] = t;
+                    P.q_cells[idx] = (int32_t)ncell;
+                    if (MODEL) atomicOr(P.qbits + (t >> 5), 1u << (t & 31));
+                } else {
+                    P.ws->queue_overflow = 1;
+                }
+            }
+        }
+    }
+}
+
+// One block: chunk_start = exclusive prefix of ceil(q_cells / chunk_cells).
+__global__ void __launch_bounds__(1024) k_chunk_scan(const DepositParams P)
+{
+    __shared__ long long part[1024];
+    Workspace *ws = P.ws;
+    if (ws->queue_overflow) {
+        if (threadIdx.x == 0) ws->n_chunk_items = 0;
+        return;
+    }
+    const int64_t q = min((int64_t)ws->queue_count, P.q_cap);
+    const int64_t per = (q + blockDim.x - 1) / blockDim.x;
+    const int64_t b = threadIdx.x * per, e = min(q, b + per);
+    const int64_t cc = P.chunk_cells;
+    long long sum = 0;
+    for (int64_t i = b; i < e; ++i) sum += (P.q_cells[i] + cc - 1) / cc;
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    // inclusive scan of the per-thread sums (Hillis-Steele)
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        const long long y = (threadIdx.x >= (unsigned)o) ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += y;
+        __syncthreads();
+    }
+    long long run = part[threadIdx.x] - sum;
+    for (int64_t i = b; i < e; ++i) {
+        P.chunk_start[i] = run;
+        run += (P.q_cells[i] + cc - 1) / cc;
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        P.chunk_start[q] = part[threadIdx.x];
+        ws->n_chunk_items = (unsigned long long)part[threadIdx.x];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -326,20 +478,46 @@ cudaError_t launch_thread_per_tet(const DepositParams &p, bool fp64, bool stats,
     return cudaGetLastError();
 }
 
-cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st)
+namespace {
+template <bool BINNED>
+cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, int64_t max_items, cudaStream_t st)
 {
     const int threads = 256;
     const size_t smem = sizeof(WarpSmem) * (threads / 32);
     const int minb = (blocks_per_sm >= 2) ? 2 : 1;
-    const void *k = stats ? (minb == 2 ? (const void *)k_warp_coop<true, 2> : (const void *)k_warp_coop<true, 1>)
-                          : (minb == 2 ? (const void *)k_warp_coop<false, 2> : (const void *)k_warp_coop<false, 1>);
+    const void *k = stats ? (minb == 2 ? (const void *)k_warp_coop<true, 2, BINNED> : (const void *)k_warp_coop<true, 1, BINNED>)
+                          : (minb == 2 ? (const void *)k_warp_coop<false, 2, BINNED> : (const void *)k_warp_coop<false, 1, BINNED>);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);
-    const int64_t need = (p.n_items + 7) / 8;
+    const int64_t need = (max_items + 7) / 8;
     if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
     void *args[] = {const_cast<DepositParams *>(&p)};
     return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
+}
+}  // namespace
+
+cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st)
+{
+    return launch_coop<false>(p, stats, blocks_per_sm, p.n_items, st);
+}
+
+cudaError_t launch_binned(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st)
+{
+    const int64_t n_tets = (p.src == SRC_TETS) ? p.n_units : 6 * p.n_units;
+    int64_t blocks = (n_tets + 127) / 128;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks < 1) blocks = 1;
+    if (p.model) k_bin_pass<true><<<(unsigned)blocks, 128, 0, st>>>(p);
+    else k_bin_pass<false><<<(unsigned)blocks, 128, 0, st>>>(p);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_chunk_scan<<<1, 1024, 0, st>>>(p);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    // the chunk count is known only on the device: size the grid for the rows plus the
+    // largest possible number of chunk items (the persistent grid is capped anyway)
+    return launch_coop<true>(p, stats, blocks_per_sm, p.n_items + p.q_cap, st);
 }
 
 cudaError_t launch_scale(double *out, int64_t n, const Workspace *ws, cudaStream_t st)

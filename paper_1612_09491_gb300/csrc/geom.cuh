@@ -302,7 +302,7 @@ PSE_HD T overlap_volume(const P3<T> (&p)[4], const P3<T> (&n)[4], T lx, T ly, T 
         // classification tolerance: a few units of rounding of this face's coordinates
         const T cmag = fmax(T(1), fmax(fmax(fmax(fabs(mnx), fabs(mxx)), fmax(fabs(mny), fabs(mxy))),
                                        fmax(fabs(mnz), fabs(mxz))));
-        const T tol = T(8) * std::numeric_limits<T>::epsilon() * cmag;
+        const T tol = T(8) * (sizeof(T) == 4 ? T(1.1920928955078125e-07) : T(2.220446049250313e-16)) * cmag;  // 8 ulp(1) x cmag
         // anchor of the between-planes region: the local origin projected onto the face plane
         const T sc = fdiv(dot(nf, a), dot(nf, nf));
         const P3<T> o = mk<T>(sc * nf.x, sc * nf.y, sc * nf.z);

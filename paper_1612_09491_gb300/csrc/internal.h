@@ -32,6 +32,10 @@ struct Workspace {
     double mass_deposited;  // sum of every computed deposit, in the grid or dropped
     int error_code;                    // first device-side error (0 = none)
     int error_detail;
+    // binned schedule
+    unsigned long long queue_count;    // split tetrahedra appended by the bin pass (may exceed q_cap)
+    unsigned long long n_chunk_items;  // work items of the split tetrahedra (0 if the queue overflowed)
+    int queue_overflow;                // 1: the queue was too small; every tetrahedron goes the row path
 };
 
 constexpr size_t kWorkspaceBytes = 512;
@@ -67,7 +71,23 @@ struct DepositParams {
     // scheduling
     int64_t n_items;
     Workspace *ws;
+    // binned schedule: tetrahedra whose bounding box has more than split_cells cells are
+    // queued by the bin pass and split into work items of chunk_cells cells
+    int64_t *q_tet;            // [q_cap] unit * 6 + s (lattice sources) or tetrahedron index
+    int32_t *q_cells;          // [q_cap] bounding-box cell count
+    int64_t *chunk_start;      // [q_cap + 1] exclusive prefix of the chunk counts
+    int64_t q_cap;
+    int32_t split_cells;       // bbox cells (no cost model) or predicted partial clips (cost model)
+    int32_t chunk_cells;
+    const struct CostModelDev *model;  // nullable: queue by the cost model's prediction
+    uint32_t *qbits;           // cost model: bit t set = tetrahedron t was queued ([ceil(T/32)])
 };
+
+// binned schedule: queue capacity and the bytes it takes after the Workspace header
+constexpr int64_t kQueueCap = int64_t(1) << 21;
+constexpr size_t kQueueBytes = ((size_t)kQueueCap * (8 + 4) + (size_t)(kQueueCap + 1) * 8 + 255) / 256 * 256;
+// cost-model binning: one bit per tetrahedron after the queue
+inline size_t qbits_bytes(int64_t n_tets) { return ((size_t)(n_tets + 31) / 32 * 4 + 255) / 256 * 256; }
 
 // message returned by pse_last_error() on this host thread (abi.cu)
 void set_last_error(const char *msg);
@@ -75,6 +95,19 @@ void set_last_error(const char *msg);
 // launchers (deposit.cu)
 cudaError_t launch_thread_per_tet(const DepositParams &p, bool fp64, bool stats, cudaStream_t st);
 cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st);
+cudaError_t launch_binned(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st);
+
+// cost model (costmodel.cu)
+struct CostModelDev;
+size_t costmodel_bytes();
+cudaError_t launch_tet_counts(const DepositParams &p, int32_t *counts, cudaStream_t st);
+cudaError_t launch_features(const DepositParams &p, float *feat, cudaStream_t st);
+cudaError_t launch_predict(const CostModelDev *m, const float *feat, int64_t n, float *out, cudaStream_t st);
+cudaError_t launch_refresh(CostModelDev *m, bool bump, cudaStream_t st);
+cudaError_t launch_train_step(CostModelDev *m, const float *feat, const float *target, const int64_t *index,
+                              int64_t batch, float lr, bool fp32, bool update, double *loss, cudaStream_t st);
+cudaError_t costmodel_set(CostModelDev *m, const float *h_params, cudaStream_t st);
+cudaError_t costmodel_get(const CostModelDev *m, float *h_params, float *h_grad, cudaStream_t st);
 cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStream_t st);
 cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread_per_tet, bool stats,
                                   int blocks_per_sm, cudaStream_t st);

@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
                                 S->lx[lane] = ts.lx;
                                 S->ly[lane] = ts.ly;
                                 S->guard[lane] = guard;
+                                S->skip[lane] = 0;
                                 if (guard) store_residuals(S, lane, res);
                             }
                         }

@@ -52,6 +52,8 @@ int main(void) {
          offsetof(pse_deposit_opts, d_cube_ids), offsetof(pse_deposit_opts, n_cube_ids));
   printf("%zu %zu %zu\n", sizeof(pse_deposit_stats), offsetof(pse_deposit_stats, bin_counts),
          offsetof(pse_deposit_stats, mass_dropped));
+  printf("%zu %zu %zu %zu\n", sizeof(pse_tuning), offsetof(pse_tuning, split_cells),
+         offsetof(pse_tuning, chunk_cells), offsetof(pse_tuning, use_graph));
   return 0;
 }
 ''')
@@ -63,6 +65,8 @@ int main(void) {
     assert got[0] == [ctypes.sizeof(La), La.particle_mass.offset, La.periodic.offset, La.box.offset]
     assert got[1] == [ctypes.sizeof(O), O.guard_eps.offset, O.d_cube_ids.offset, O.n_cube_ids.offset]
     assert got[2] == [ctypes.sizeof(S), S.bin_counts.offset, S.mass_dropped.offset]
+    Tu = _lib.Tuning
+    assert got[3] == [ctypes.sizeof(Tu), Tu.split_cells.offset, Tu.chunk_cells.offset, Tu.use_graph.offset]
 
 
 def test_abi_version(L):
@@ -105,6 +109,12 @@ def test_invalid_arguments_return_codes(L):
 def test_workspace_size(L):
     assert L.pse_workspace_size(_lib.PSE_OP_DEPOSIT_UNIFORM, None, None) >= 64
     assert L.pse_workspace_size(12345, None, None) == 0
+    # the binned schedule needs room for its queue of split tetrahedra
+    import paper_1612_09491_gb300 as pse
+    plain = pse.workspace_size(_lib.PSE_OP_DEPOSIT_UNIFORM, schedule=_lib.PSE_WARP_COOPERATIVE)
+    binned = pse.workspace_size(_lib.PSE_OP_DEPOSIT_UNIFORM, schedule=_lib.PSE_BINNED_PERSISTENT)
+    assert plain == L.pse_workspace_size(_lib.PSE_OP_DEPOSIT_UNIFORM, None, None)
+    assert binned > plain + (1 << 20)
 
 
 def test_octree_leaf_validation_needs_no_gpu(L):

@@ -32,7 +32,17 @@ PATHS = [
     ("fp64-thread", pse.PSE_FP64_PLAIN, pse.PSE_THREAD_PER_TET),
     ("fp32-thread", pse.PSE_FP32_FP64ACC, pse.PSE_THREAD_PER_TET),
     ("fp32-warp", pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE),
+    ("fp32-binned", pse.PSE_FP32_FP64ACC, "binned"),
 ]
+# the binned schedule with tiny thresholds, so that small cases go through the split
+# work items (every tetrahedron with more than 4 bounding-box cells, 8 cells per item)
+SPLIT_TUNING = {"split_cells": 4, "chunk_cells": 8}
+
+
+def sched_kw(sched):
+    if sched == "binned":
+        return {"schedule": pse.PSE_BINNED_PERSISTENT, "tuning": SPLIT_TUNING}
+    return {"schedule": sched}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -52,7 +62,7 @@ def dev(a, dtype=None):
 
 
 def gpu_lattice(pos, n, g, prec, sched, **kw):
-    out = pse.deposit_uniform(dev(pos), n, g, precision=prec, schedule=sched, **kw)
+    out = pse.deposit_uniform(dev(pos), n, g, precision=prec, **sched_kw(sched), **kw)
     if isinstance(out, tuple):
         return out[0].cpu().numpy(), out[1]
     return out.cpu().numpy()
@@ -60,7 +70,7 @@ def gpu_lattice(pos, n, g, prec, sched, **kw):
 
 def gpu_tets(verts, mass, g, prec, sched, **kw):
     out = pse.deposit_tets(dev(np.asarray(verts, np.float32)), dev(np.asarray(mass, np.float64)), g,
-                           precision=prec, schedule=sched, **kw)
+                           precision=prec, **sched_kw(sched), **kw)
     if isinstance(out, tuple):
         return out[0].cpu().numpy(), out[1]
     return out.cpu().numpy()
@@ -206,6 +216,47 @@ def test_config1_full(name, prec, sched):
     assert abs(st["mass_in"] - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("tuning", [None, SPLIT_TUNING, {"split_cells": 64, "chunk_cells": 1000}])
+def test_binned_counts_match_warp_cooperative(tuning):
+    """The binned schedule visits exactly the pairs of the warp-cooperative one (the counters
+    are deterministic), whatever its split thresholds.  The masses agree to FP32 rounding:
+    the two kernels are compiled separately and may fuse multiply-adds differently."""
+    cfg = CONFIGS[1]
+    dpos = dev(config_positions(cfg))
+    a, sa = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, schedule=pse.PSE_WARP_COOPERATIVE, stats=True)
+    b, sb = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, schedule=pse.PSE_BINNED_PERSISTENT, tuning=tuning,
+                                stats=True)
+    for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos", "single_cell_tets",
+              "bin_counts"):
+        assert sa[k] == sb[k], k
+    e = cell_errors(b.cpu().numpy(), a.cpu().numpy())
+    assert e["max_rel"] <= 2e-6, e
+    assert e["mass"] <= 1e-13, e
+
+
+def test_binned_graph_replay():
+    """use_graph: the launch sequence is captured once per argument set and replayed; replays
+    read the current contents of the buffers, and other arguments capture a new graph."""
+    n, g = 16, 32
+    p1 = dev(zeldovich_positions(n, -2.0, 1.5, seed=21))
+    p2 = zeldovich_positions(n, -2.0, 1.5, seed=22)
+    ws = torch.empty(pse.workspace_size(schedule=pse.PSE_BINNED_PERSISTENT), dtype=torch.uint8, device="cuda")
+    tu = dict(SPLIT_TUNING, use_graph=1)
+    plain = lambda pos: pse.deposit_uniform(pos, n, g, schedule=pse.PSE_BINNED_PERSISTENT,
+                                            tuning=SPLIT_TUNING).cpu().numpy()
+    out = torch.empty((g, g, g), dtype=torch.float64, device="cuda")
+    ref1 = plain(p1)
+    for _ in range(3):
+        pse.deposit_uniform(p1, n, g, out=out, workspace=ws, schedule=pse.PSE_BINNED_PERSISTENT, tuning=tu)
+        assert cell_errors(out.cpu().numpy(), ref1)["max_rel"] <= 1e-12
+    p1.copy_(torch.from_numpy(p2))  # same pointer, new contents
+    pse.deposit_uniform(p1, n, g, out=out, workspace=ws, schedule=pse.PSE_BINNED_PERSISTENT, tuning=tu)
+    assert cell_errors(out.cpu().numpy(), plain(p1))["max_rel"] <= 1e-12
+    out2 = torch.empty_like(out)  # another output buffer: another graph
+    pse.deposit_uniform(p1, n, g, out=out2, workspace=ws, schedule=pse.PSE_BINNED_PERSISTENT, tuning=tu)
+    assert cell_errors(out2.cpu().numpy(), plain(p1))["max_rel"] <= 1e-12
+
+
 @pytest.mark.parametrize("name,prec,sched", PATHS)
 def test_shell_crossed_small(name, prec, sched):
     """Strong shell crossing (rms 3 spacings, many inverted and sliver tetrahedra), 16^3 particles."""
@@ -268,11 +319,12 @@ def test_cube_subset_and_accumulate(name, prec, sched):
     ref_a, _ = oracle.deposit_lattice(pos, n, g, cube_ids=a_ids)
     ref, _ = oracle.deposit_lattice(pos, n, g)
     dpos = dev(pos)
-    out = pse.deposit_uniform(dpos, n, g, precision=prec, schedule=sched, cube_ids=dev(a_ids))
+    out = pse.deposit_uniform(dpos, n, g, precision=prec, **sched_kw(sched), cube_ids=dev(a_ids))
     fl = density_floor(subset_tets(pos, n, a_ids), np.full(6 * len(a_ids), 1.0 / (6 * n ** 3)), g)
     e = cell_errors(out.cpu().numpy(), ref_a, floor_mass=fl)
     assert e["max_rel"] <= tol_for(prec), e
-    pse.deposit_uniform(dpos, n, g, precision=prec, schedule=sched, cube_ids=dev(b_ids), out=out, accumulate=True)
+    pse.deposit_uniform(dpos, n, g, precision=prec, **sched_kw(sched), cube_ids=dev(b_ids), out=out,
+                        accumulate=True)
     e = cell_errors(out.cpu().numpy(), ref)
     assert e["max_rel"] <= tol_for(prec), e
 
