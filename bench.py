@@ -43,6 +43,7 @@ FLOP_PER_TET = 150.0
 FLOP_PER_BBOX_CELL = 32.0
 FLOP_PER_CLIP = 620.0
 SM_COUNT_GB300 = 152
+PRECISION = "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up"
 FP32_LANES_PER_SM = 128
 
 
@@ -186,6 +187,190 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------- other workloads --
+def _timed(step, steps, warmup, flush, stream):
+    """CUDA-event times (ms) of `steps` calls of step() after `warmup` untimed ones, L2 flushed between."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_workload(args, cfg):
+    """Workloads 3 (octree), 4 (uniform 512^3 with the learned cost model) and 5 (octree over a
+    1024^3 lattice streamed from pinned host memory in z-slabs).  One JSON line, like main()."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_09491_gb300 as pse
+    from paper_1612_09491_gb300 import autotune
+    from paper_1612_09491_gb300 import costmodel as cm
+    from paper_1612_09491_gb300.metrics import cell_errors
+    from pse_inputs import CONFIGS, config_positions, zeldovich_positions_device
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    prec = pse.PSE_FP32_FP64ACC
+    n = cfg.n
+    t0 = time.perf_counter()
+    if n <= 256:
+        pos = torch.from_numpy(config_positions(cfg)).to(dev)
+        gen = "numpy PCG64 + FFT on the host"
+    else:
+        pos = zeldovich_positions_device(n, cfg.spectral_index, cfg.rms_disp, cfg.seed, device=dev)
+        gen = "torch generator + torch.fft on the GPU (float32)"
+    gen_s = time.perf_counter() - t0
+    extra = {"input_generation": f"{gen}, {gen_s:.1f} s"}
+    config = {"workload": cfg.name, "particles": f"{n}^3", "tets": cfg.n_tets,
+              "spectrum": f"P(k)~k^{cfg.spectral_index}", "rms_disp_spacings": cfg.rms_disp,
+              "precision": PRECISION,
+              "l2": "512 MB buffer written between timed steps", "parallelism": "replicas x1"}
+    base = None
+    if cfg.grid == "octree":
+        slab = 64
+        if cfg.index == 5:
+            # the positions live in pinned host memory; the GPU copy is dropped
+            h = torch.empty((n ** 3, 3), dtype=torch.float32).pin_memory()
+            h.copy_(pos)
+            del pos
+            torch.cuda.empty_cache()
+            t0 = time.perf_counter()
+            oct_ = pse.build_octree_streamed(h, n, cfg.bc, cfg.max_level, slab, 2.0)
+            extra["octree_build_s"] = time.perf_counter() - t0
+            out = torch.empty((oct_.n_leaves, cfg.bc, cfg.bc, cfg.bc), dtype=torch.float64, device=dev)
+
+            def step(stats=False):
+                return pse.deposit_octree_streamed(h, n, oct_, slab, out=out, stats=stats, precision=prec,
+                                                   tuning={"blocks_per_sm": 3})
+            config.update({"grid": f"octree bc={cfg.bc} levels 0-{cfg.max_level} (finest {cfg.grid_n}^3)",
+                           "schedule": "warp-cooperative", "streaming": f"z-slabs of {slab} cube layers from "
+                                                                        "pinned host memory, double-buffered"})
+            h2d = int(h.numel() * 4 * (1 + 1 / slab))
+        else:
+            t0 = time.perf_counter()
+            oct_ = pse.build_octree_from_tet_sizes(pos, n, cfg.bc, cfg.max_level, 2.0)
+            torch.cuda.synchronize()
+            extra["octree_build_s"] = time.perf_counter() - t0
+            out = torch.empty((oct_.n_leaves, cfg.bc, cfg.bc, cfg.bc), dtype=torch.float64, device=dev)
+            tuned, tune_ms = autotune.tune(lambda tu: pse.deposit_octree(pos, n, oct_, out=out, tuning=tu,
+                                                                         precision=prec),
+                                           signature=f"octree:{cfg.name}")
+            config["autotune_ms"] = tune_ms
+
+            def step(stats=False):
+                return pse.deposit_octree(pos, n, oct_, out=out, stats=stats, tuning=tuned, precision=prec)
+            config.update({"grid": f"octree bc={cfg.bc} levels 0-{cfg.max_level} (finest {cfg.grid_n}^3)",
+                           "schedule": "warp-cooperative", "tuning": tuned})
+            h2d = 0
+        config["leaves"] = int(oct_.n_leaves)
+        config["leaf_levels"] = {int(l): int(c) for l, c in zip(*np.unique(oct_.leaves()[:, 0], return_counts=True))}
+        _, st = step(stats=True)
+        grid_cells = oct_.n_cells
+    else:
+        g = cfg.grid_n
+        out = torch.empty((g, g, g), dtype=torch.float64, device=dev)
+        ws = torch.empty(pse.workspace_size(pse._lib.PSE_OP_DEPOSIT_UNIFORM, pse.lattice(n),
+                                            schedule=pse.PSE_BINNED_PERSISTENT, cost_model=cm.CostModel()),
+                         dtype=torch.uint8, device=dev)
+        # the cost model, trained on the counts the exact deposit produces on workloads 1 and 2
+        t0 = time.perf_counter()
+        feats, targs = [], []
+        for c in (CONFIGS[1], CONFIGS[2]):
+            p = torch.from_numpy(config_positions(c)).to(dev)
+            feats.append(cm.features(p, c.n, c.grid_n))
+            targs.append(cm.labels(cm.tet_counts(p, c.n, c.grid_n)))
+        feat, targ = torch.cat(feats), torch.cat(targs)
+        mu, sd = cm.standardisation(feat[:: max(1, feat.shape[0] // 200000)].cpu().numpy())
+        model = cm.CostModel(cm.pack({**cm.he_init(0), "mu": mu, "sigma": sd}))
+        hist = cm.fit(model, feat, targ, steps=2000, batch=8192, lr=3e-3)
+        extra["cost_model"] = {"training_s": time.perf_counter() - t0, "loss_first_last": [hist[0], hist[-1]],
+                               "train_rows": int(feat.shape[0])}
+        del feat, targ, feats, targs
+        arms = {"warp": dict(schedule=pse.PSE_WARP_COOPERATIVE, tuning={"blocks_per_sm": 3}, precision=prec),
+                "binned-bbox": dict(schedule=pse.PSE_BINNED_PERSISTENT, precision=prec,
+                                    tuning={"blocks_per_sm": 3, "split_cells": 512, "chunk_cells": 512}),
+                "binned-model": dict(schedule=pse.PSE_BINNED_PERSISTENT, cost_model=model, precision=prec,
+                                     tuning={"blocks_per_sm": 3, "split_cells": 256, "chunk_cells": 512})}
+        arm_ms = {}
+        for name, kw in arms.items():
+            ms_list = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, **kw), max(1, args.steps),
+                             1, flush, stream)
+            arm_ms[name] = sum(ms_list) / len(ms_list)
+        extra["arms_ms"] = arm_ms
+        chosen = arms["binned-model"]
+
+        def step(stats=False):
+            return pse.deposit_uniform(pos, n, g, out=out, workspace=ws, stats=stats, **chosen)
+        config.update({"grid": f"uniform {g}^3 float64", "schedule": "binned persistent, cost-model split",
+                       "tuning": chosen["tuning"]})
+        h2d = 0
+        _, st = step(stats=True)
+        grid_cells = g ** 3
+        # the plain FP64 one-thread-per-tetrahedron path, on a 1/64 sample of the cubes
+        ids = torch.from_numpy(np.sort(np.random.default_rng(5).choice(n ** 3, n ** 3 // 64,
+                                                                       replace=False))).to(dev)
+        bms = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, precision=pse.PSE_FP64_PLAIN,
+                                                 schedule=pse.PSE_THREAD_PER_TET, cube_ids=ids), 1, 1, flush, stream)[0]
+        fast = pse.deposit_uniform(pos, n, g, cube_ids=ids, **{k: v for k, v in chosen.items()
+                                                               if k != "cost_model"}).cpu().numpy()
+        slow = out.cpu().numpy()
+        base = {"tets_per_s": 6 * ids.numel() / (bms * 1e-3), "sample": "1/64 of the cubes (random, seed 5)",
+                "error_of_timed_arm_on_sample": cell_errors(fast, slow)}
+
+    with ClockSampler(bus_id_of(0)) as clk:
+        t_wall0 = time.perf_counter()
+        step_ms = _timed(step, args.steps, args.warmup, flush, stream)
+        t_wall = time.perf_counter() - t_wall0
+    ms = sum(step_ms) / len(step_ms)
+    value = cfg.n_tets / (ms * 1e-3)
+    mass_error = abs(float(out.sum()) - 1.0)
+    if base is None and cfg.index == 3:
+        fast = out.cpu().numpy()
+        bms = _timed(lambda: pse.deposit_octree(pos, n, oct_, out=out, precision=pse.PSE_FP64_PLAIN,
+                                                schedule=pse.PSE_THREAD_PER_TET), 1, 1, flush, stream)[0]
+        base = {"tets_per_s": cfg.n_tets / (bms * 1e-3), "ms_per_step": bms,
+                "error_of_timed_arm": cell_errors(fast, out.cpu().numpy())}
+    if base is not None:
+        base["speedup"] = value / base["tets_per_s"]
+    csum = clk.summary()
+    max_mhz = csum.get("sm_max_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count or SM_COUNT_GB300
+    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    alg = FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] + FLOP_PER_CLIP * st["partial_clips"]
+    achieved = alg / (ms * 1e-3) / 1e12
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config,
+        "clips_per_s": st["partial_clips"] / (ms * 1e-3),
+        "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
+                                        "degenerate_tets", "single_cell_tets")},
+        "mass_error": mass_error,
+        "fp64_gpu_baseline": base,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "note": "step time (all kernels of the call)",
+                     "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 0,
+                "note": "streamed from pinned host memory inside the step" if h2d else
+                        "inputs resident (no host copies in this workload's step)"},
+        "grid_cells": int(grid_cells), "clocks": csum, "wall_s_timed": t_wall, **extra,
+    }
+    print(json.dumps(result), flush=True)
+
+
 # ---------------------------------------------------------------- ours ------
 def main():
     args = parse()
@@ -193,6 +378,9 @@ def main():
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
         run_reference(args, cfg)
+        return
+    if args.config >= 3:
+        run_workload(args, cfg)
         return
 
     import numpy as np
@@ -228,13 +416,14 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     from paper_1612_09491_gb300 import autotune
+    prec = pse.PSE_FP32_FP64ACC
 
     def call(tu, **kw):
         """One deposit with an autotuner candidate {"schedule": "warp" | "binned", knobs...}."""
         knobs = {k: v for k, v in tu.items() if k != "schedule"}
         sched = pse.PSE_BINNED_PERSISTENT if tu["schedule"] == "binned" else pse.PSE_WARP_COOPERATIVE
-        return pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=pse.PSE_FP32_FP64ACC,
-                                   schedule=sched, tuning=knobs, **kw)
+        return pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=prec, schedule=sched, tuning=knobs,
+                                   **kw)
 
     tuned, tune_ms = autotune.tune(call, signature=f"uniform:{cfg.name}", candidates=autotune.UNIFORM_CANDIDATES)
 
@@ -340,7 +529,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg.name, "particles": f"{n}^3", "tets": n_tets, "grid": f"uniform {g}^3 float64",
                        "spectrum": f"P(k)~k^{cfg.spectral_index}", "rms_disp_spacings": cfg.rms_disp,
-                       "precision": "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up",
+                       "precision": PRECISION,
                        "schedule": {"binned": "binned persistent", "warp": "warp-cooperative"}[tuned["schedule"]],
                        "tuning": tuned, "autotune_ms": tune_ms,
                        "l2": "512 MB buffer written between timed steps",

@@ -146,8 +146,8 @@ typedef struct pse_octree {
 } pse_octree;
 
 typedef struct pse_tuning {
-    int32_t blocks_per_sm;   /* resident blocks per SM of the warp-cooperative kernels: 1 (no register
-                                cap) or 2 (128 registers per thread); <= 0: the built-in default */
+    int32_t blocks_per_sm;   /* resident 128-thread blocks per SM of the warp-cooperative kernels: 2 (up
+                                to 255 registers per thread), 3 (170) or 4 (128); <= 0: 2 */
     int32_t warps_per_block; /* reserved (8) */
     int32_t split_cells;     /* binned schedule: a tetrahedron whose bounding box has more cells than
                                 this is split across warps; <= 0: default 1024 */
@@ -261,6 +261,31 @@ PSE_API void pse_free_octree(pse_octree *oct);
 PSE_API int pse_build_octree_leaves_noalloc(const float *d_pos, const pse_lattice *lat, int32_t bc,
                                             int32_t max_level, double edge_threshold_cells, int32_t *d_leaves,
                                             int64_t cap, int64_t *d_n_leaves, void *stream);
+
+/*
+ * Slab streaming (periodic lattices whose positions live in host memory): the lattice
+ * is deposited in z-slabs of slab_cubes cube layers.  Each slab's slab_cubes + 1 particle
+ * rows (the last one a halo row, taken modulo n2) are copied into one of two device
+ * buffers while the previous slab is deposited (double buffering on a second stream).
+ * The result equals the one-shot deposit of the whole lattice (same cube set).
+ *   h_pos       host float32 [n0*n1*n2][3]; pinned memory lets the copies overlap the
+ *               kernels (pageable memory works, without overlap).
+ *   slab_cubes  cube layers per slab (>= 1).
+ * The other arguments are those of pse_deposit_uniform / pse_deposit_octree
+ * (opts->d_cube_ids must be NULL and use_graph 0).  The statistics and the FP32 mass
+ * renormalisation cover the whole lattice.  The calls allocate two slab buffers
+ * (stream-ordered) and do not synchronise unless h_stats is given.
+ */
+PSE_API int pse_deposit_uniform_streamed(const float *h_pos, const pse_lattice *lat, int64_t slab_cubes,
+                                         const int64_t grid_n[3], double *d_cell_mass, const pse_deposit_opts *opts,
+                                         pse_deposit_stats *h_stats, void *d_ws, size_t ws_bytes, void *stream);
+PSE_API int pse_deposit_octree_streamed(const float *h_pos, const pse_lattice *lat, int64_t slab_cubes,
+                                        const pse_octree *oct, double *d_leaf_mass, const pse_deposit_opts *opts,
+                                        pse_deposit_stats *h_stats, void *d_ws, size_t ws_bytes, void *stream);
+/* pse_build_octree_from_tet_sizes over a streamed lattice (histograms accumulated slab
+ * by slab).  Synchronous, like the one-shot build. */
+PSE_API int pse_build_octree_streamed(const float *h_pos, const pse_lattice *lat, int64_t slab_cubes, int32_t bc,
+                                      int32_t max_level, double edge_threshold_cells, pse_octree *out, void *stream);
 
 /*
  * Learned cost model of the binned schedule (the paper has none: it balances work by

@@ -21,7 +21,7 @@ from ._lib import (  # noqa: F401
 
 __all__ = ["build_tets_from_lagrangian_grid", "deposit_uniform", "deposit_tets", "workspace_size", "last_error",
            "abi_version", "lattice", "opts", "OctreeHandle", "octree_from_leaves", "build_octree_from_tet_sizes",
-           "deposit_octree"]
+           "deposit_octree", "deposit_uniform_streamed", "deposit_octree_streamed", "build_octree_streamed"]
 
 
 _EMPTY_SENTINEL = 16  # non-NULL, never dereferenced (n_cube_ids == 0)
@@ -262,3 +262,71 @@ def deposit_octree(pos, n, octree: OctreeHandle, *, box: float = 1.0, particle_m
                               ctypes.byref(st) if st is not None else None, ws_ptr, ws_bytes, _stream_ptr(stream))
     _lib.check(rc)
     return (out, st.to_dict()) if stats else out
+
+
+def _host_ptr(t, name):
+    """Pointer of a contiguous float32 CPU tensor or numpy array (host memory)."""
+    torch = _torch()
+    import numpy as np
+    if isinstance(t, torch.Tensor):
+        if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float32 CPU tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    if not isinstance(t, np.ndarray) or t.dtype != np.float32 or not t.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"{name} must be a contiguous float32 array")
+    return ctypes.c_void_p(t.ctypes.data)
+
+
+def deposit_uniform_streamed(h_pos, n, grid_n, slab_cubes: int, *, box: float = 1.0, particle_mass=None, out=None,
+                             device="cuda", precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE,
+                             guard_eps: float = 0.0, accumulate: bool = False, mass_fixup: bool = True,
+                             stats: bool = False, workspace=None, stream=None, tuning=None, cost_model=None):
+    """pse_deposit_uniform_streamed: positions in host memory (pinned for overlap), z-slabs of slab_cubes."""
+    torch = _torch()
+    L = _lib.load()
+    lat = lattice(n, box, True, particle_mass)
+    g3, g = _grid3(grid_n)
+    if out is None:
+        out = torch.empty((g[2], g[1], g[0]), dtype=torch.float64, device=device)
+    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, None, tuning, cost_model)
+    st = _lib.DepositStats() if stats else None
+    ws_ptr, ws_bytes = (ctypes.c_void_p(None), 0) if workspace is None else \
+        (_dev_ptr(workspace, torch.uint8, "workspace"), workspace.numel())
+    _lib.check(L.pse_deposit_uniform_streamed(_host_ptr(h_pos, "h_pos"), ctypes.byref(lat), int(slab_cubes), g3,
+                                              _dev_ptr(out, torch.float64, "out"), ctypes.byref(o),
+                                              ctypes.byref(st) if st is not None else None, ws_ptr, ws_bytes,
+                                              _stream_ptr(stream)))
+    return (out, st.to_dict()) if stats else out
+
+
+def deposit_octree_streamed(h_pos, n, octree: OctreeHandle, slab_cubes: int, *, box: float = 1.0,
+                            particle_mass=None, out=None, device="cuda", precision: int = PSE_FP32_FP64ACC,
+                            schedule: int = PSE_WARP_COOPERATIVE, guard_eps: float = 0.0, accumulate: bool = False,
+                            mass_fixup: bool = True, stats: bool = False, workspace=None, stream=None, tuning=None):
+    """pse_deposit_octree_streamed: leaf masses [n_leaves, bc, bc, bc] from host positions in z-slabs."""
+    torch = _torch()
+    L = _lib.load()
+    lat = lattice(n, box, True, particle_mass)
+    bc = octree.bc
+    if out is None:
+        out = torch.empty((octree.n_leaves, bc, bc, bc), dtype=torch.float64, device=device)
+    o = opts(precision, schedule, guard_eps, accumulate, mass_fixup, None, tuning)
+    st = _lib.DepositStats() if stats else None
+    ws_ptr, ws_bytes = (ctypes.c_void_p(None), 0) if workspace is None else \
+        (_dev_ptr(workspace, torch.uint8, "workspace"), workspace.numel())
+    _lib.check(L.pse_deposit_octree_streamed(_host_ptr(h_pos, "h_pos"), ctypes.byref(lat), int(slab_cubes),
+                                             ctypes.byref(octree.st), _dev_ptr(out, torch.float64, "out"),
+                                             ctypes.byref(o), ctypes.byref(st) if st is not None else None, ws_ptr,
+                                             ws_bytes, _stream_ptr(stream)))
+    return (out, st.to_dict()) if stats else out
+
+
+def build_octree_streamed(h_pos, n, bc: int, max_level: int, slab_cubes: int, threshold_cells: float = 2.0, *,
+                          box: float = 1.0, stream=None) -> OctreeHandle:
+    """pse_build_octree_streamed: the size-rule octree of a lattice held in host memory."""
+    lat = lattice(n, box, True)
+    st = _lib.Octree()
+    _lib.check(_lib.load().pse_build_octree_streamed(_host_ptr(h_pos, "h_pos"), ctypes.byref(lat), int(slab_cubes),
+                                                     bc, max_level, float(threshold_cells), ctypes.byref(st),
+                                                     _stream_ptr(stream)))
+    return OctreeHandle(st)

@@ -47,6 +47,9 @@ EXPORTED = (
     "pse_deposit_octree",
     "pse_free_octree",
     "pse_build_octree_leaves_noalloc",
+    "pse_deposit_uniform_streamed",
+    "pse_deposit_octree_streamed",
+    "pse_build_octree_streamed",
     "pse_costmodel_bytes",
     "pse_costmodel_set",
     "pse_costmodel_get",
@@ -141,6 +144,17 @@ def load(build_if_missing: bool = False):
         L.pse_build_octree_leaves_noalloc.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int32, ctypes.c_int32,
                                                       ctypes.c_double, vp, ctypes.c_int64, vp, vp]
         L.pse_build_octree_leaves_noalloc.restype = ctypes.c_int
+        L.pse_deposit_uniform_streamed.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int64,
+                                                   ctypes.POINTER(ctypes.c_int64), vp, ctypes.POINTER(DepositOpts),
+                                                   ctypes.POINTER(DepositStats), vp, ctypes.c_size_t, vp]
+        L.pse_deposit_uniform_streamed.restype = ctypes.c_int
+        L.pse_deposit_octree_streamed.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int64, OP, vp,
+                                                  ctypes.POINTER(DepositOpts), ctypes.POINTER(DepositStats), vp,
+                                                  ctypes.c_size_t, vp]
+        L.pse_deposit_octree_streamed.restype = ctypes.c_int
+        L.pse_build_octree_streamed.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int64, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_double, OP, vp]
+        L.pse_build_octree_streamed.restype = ctypes.c_int
         L.pse_costmodel_bytes.argtypes = []
         L.pse_costmodel_bytes.restype = ctypes.c_size_t
         L.pse_costmodel_set.argtypes = [vp, vp, vp]

@@ -10,13 +10,14 @@ from __future__ import annotations
 import json
 import os
 
-CANDIDATES = ({"blocks_per_sm": 1}, {"blocks_per_sm": 2})
+# residency: resident 128-thread blocks per SM (2: 255 registers, 3: 170, 4: 128)
+CANDIDATES = ({"blocks_per_sm": 2}, {"blocks_per_sm": 3}, {"blocks_per_sm": 4})
 # uniform-grid deposits: the warp-cooperative kernel, and the binned persistent schedule
 # over its split threshold, split work-item size and residency (launched as a CUDA graph)
-UNIFORM_CANDIDATES = tuple([{"schedule": "warp", "blocks_per_sm": b} for b in (1, 2)] +
+UNIFORM_CANDIDATES = tuple([{"schedule": "warp", "blocks_per_sm": b} for b in (2, 3, 4)] +
                            [{"schedule": "binned", "blocks_per_sm": b, "split_cells": sp, "chunk_cells": ch,
                              "use_graph": 1}
-                            for b in (1, 2) for sp in (256, 1024, 4096) for ch in (256, 1024)])
+                            for b in (2, 3) for sp in (256, 2048) for ch in (256, 1024)])
 _mem = {}
 
 

@@ -4,6 +4,8 @@
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -55,7 +57,7 @@ pse_deposit_opts default_opts()
 constexpr double kDefaultGuardEps = 1.0e-5;
 
 // resident blocks per SM of the warp-cooperative kernel (1: no register cap; 2: 128 registers)
-constexpr int kDefaultBlocksPerSm = 1;
+constexpr int kDefaultBlocksPerSm = 2;  // 128-thread blocks: 255 registers per thread
 
 float kappa_limit(double guard_eps)
 {
@@ -138,7 +140,7 @@ int check_opts(const pse_deposit_opts &o)
         return fail(PSE_ERR_INVALID_ARG, "unknown precision %d", o.precision);
     if (o.schedule != PSE_THREAD_PER_TET && o.schedule != PSE_WARP_COOPERATIVE && o.schedule != PSE_BINNED_PERSISTENT)
         return fail(PSE_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
-    if (o.schedule != PSE_THREAD_PER_TET && o.precision != PSE_FP32_FP64ACC)
+    if (o.schedule != PSE_THREAD_PER_TET && o.precision == PSE_FP64_PLAIN)
         return fail(PSE_ERR_UNSUPPORTED, "the warp-cooperative and binned schedules run the FP32 clip (precision 1)");
     if (o.n_cube_ids < 0) return fail(PSE_ERR_INVALID_ARG, "n_cube_ids < 0");
     if (o.n_cube_ids > 0 && !o.d_cube_ids) return fail(PSE_ERR_INVALID_ARG, "n_cube_ids > 0 but d_cube_ids is NULL");
@@ -154,6 +156,76 @@ void fill_grid(pse::DepositParams &p, const int64_t grid_n[3], double box)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Slab streaming: the particle lattice stays in host memory and is copied to the GPU
+// one z-slab at a time (slab_cubes cube layers = slab_cubes + 1 particle rows, the last
+// one the halo row, taken modulo n2), double-buffered: the copy of slab s + 1 runs on a
+// second stream while the kernels of slab s run on `st`.  per_slab(p, st) enqueues the
+// work of one slab, p describing it in slab mode.
+// ---------------------------------------------------------------------------
+template <class F>
+int stream_slabs(const float *h_pos, const pse::DepositParams &base, int64_t slab_cubes, cudaStream_t st, F per_slab)
+{
+    const int64_t n0 = base.n[0], n1 = base.n[1], n2 = base.n[2];
+    const size_t row = (size_t)n0 * (size_t)n1 * 3;  // floats per particle row
+    const int64_t nslab = (n2 + slab_cubes - 1) / slab_cubes;
+    const size_t buf_bytes = (size_t)(slab_cubes + 1) * row * sizeof(float);
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ready = nullptr, copied[2] = {nullptr, nullptr}, freed[2] = {nullptr, nullptr};
+    float *buf[2] = {nullptr, nullptr};
+    int rc = PSE_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&freed[b], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&buf[b]), buf_bytes, st);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ready, st);  // the buffers exist once st gets here
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ready, 0);
+    if (e != cudaSuccess) rc = (e == cudaErrorMemoryAllocation) ? fail(PSE_ERR_OOM, "slab buffers: %s",
+                                                                        cudaGetErrorString(e))
+                                                               : cuda_fail(e, "slab stream set-up");
+    for (int64_t sl = 0; sl < nslab && rc == PSE_OK; ++sl) {
+        const int b = (int)(sl & 1);
+        const int64_t k0 = sl * slab_cubes, k1 = std::min(n2, k0 + slab_cubes);
+        if (sl >= 2) e = cudaStreamWaitEvent(cs, freed[b], 0);  // slab sl - 2 no longer reads buf[b]
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(buf[b], h_pos + (size_t)k0 * row, (size_t)(k1 - k0) * row * sizeof(float),
+                                cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess)  // halo row
+            e = cudaMemcpyAsync(buf[b] + (size_t)(k1 - k0) * row, h_pos + (size_t)(k1 % n2) * row, row * sizeof(float),
+                                cudaMemcpyHostToDevice, cs);
+        if (e == cudaSuccess) e = cudaEventRecord(copied[b], cs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, copied[b], 0);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "slab copy");
+            break;
+        }
+        pse::DepositParams p = base;
+        p.pos = buf[b];
+        p.slab = 1;
+        p.n[2] = k1 - k0 + 1;
+        p.nc[2] = k1 - k0;
+        p.src = pse::SRC_LATTICE;
+        p.n_units = p.nc[0] * p.nc[1] * p.nc[2];
+        p.n_items = ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2];
+        rc = per_slab(p, st);
+        if (rc != PSE_OK) break;
+        e = cudaEventRecord(freed[b], st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "slab event");
+    }
+    // st finishes every kernel after the copies it waited for, so the buffers can go
+    for (int b = 0; b < 2; ++b) {
+        if (buf[b]) cudaFreeAsync(buf[b], st);
+        if (copied[b]) cudaEventDestroy(copied[b]);
+        if (freed[b]) cudaEventDestroy(freed[b]);
+    }
+    if (ready) cudaEventDestroy(ready);
+    if (cs) cudaStreamDestroy(cs);
+    return rc;
+}
+
 constexpr int kDefaultSplitCells = 1024;
 constexpr int kDefaultChunkCells = 512;
 
@@ -166,15 +238,19 @@ size_t deposit_ws_bytes(const pse_deposit_opts *o, int64_t n_tets)
     return pse::kWorkspaceBytes + pse::kQueueBytes + pse::qbits_bytes(n_tets);
 }
 
+// h_pos != NULL: stream the lattice from host memory in z-slabs of slab_cubes cube layers
 int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells, pse_deposit_stats *h_stats,
-                void *d_ws, size_t ws_bytes, cudaStream_t st)
+                void *d_ws, size_t ws_bytes, cudaStream_t st, const float *h_pos = nullptr, int64_t slab_cubes = 0)
 {
     const bool binned = o.schedule == PSE_BINNED_PERSISTENT && !p.leaves;
     const pse_tuning *tu = static_cast<const pse_tuning *>(o.tuning);
     const bool stats = h_stats != nullptr;
-    const bool graph = binned && tu && tu->use_graph && d_ws != nullptr && !stats;
+    const bool streamed = h_pos != nullptr;
+    const bool graph = binned && tu && tu->use_graph && d_ws != nullptr && !stats && !streamed;
     WsLease lease;
-    const int64_t n_tets = (p.src == pse::SRC_TETS) ? p.n_units : 6 * p.n_units;
+    // streamed: tetrahedron ids (cost-model bitmap) are slab-local
+    const int64_t n_tets = streamed ? 6 * p.nc[0] * p.nc[1] * std::min(slab_cubes, p.nc[2])
+                                    : (p.src == pse::SRC_TETS) ? p.n_units : 6 * p.n_units;
     int rc = acquire_ws(d_ws, ws_bytes, st, lease, deposit_ws_bytes(&o, n_tets), false);
     if (rc != PSE_OK) return rc;
     p.ws = lease.ws;
@@ -198,17 +274,33 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
     p.kappa_max = kappa_limit(o.guard_eps);
     // FP32 mass renormalisation: the call's deposits are scaled by sum(m_t)/sum(deposits);
     // it needs the output to hold this call's deposits only (accumulate = 0)
-    const bool renorm = o.mass_fixup && !o.accumulate && o.precision == PSE_FP32_FP64ACC;
+    const bool renorm = o.mass_fixup && !o.accumulate && o.precision != PSE_FP64_PLAIN;
     p.fixup = renorm ? 1 : 0;
     const int bps = (tu && tu->blocks_per_sm > 0) ? tu->blocks_per_sm : kDefaultBlocksPerSm;
     if (p.n_units > 0 && o.schedule != PSE_THREAD_PER_TET)
         p.n_items = (p.src == pse::SRC_LATTICE) ? ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2] : (p.n_units + 31) / 32;
 
+    // the kernels of one deposit pass over the tetrahedra of q, on stream s
+    auto launch = [&](const pse::DepositParams &q, cudaStream_t s) -> int {
+        if (q.n_units <= 0) return PSE_OK;
+        cudaError_t e;
+        if (q.leaves) {
+            e = pse::launch_octree_deposit(q, o.precision == PSE_FP64_PLAIN, o.schedule == PSE_THREAD_PER_TET, stats,
+                                           bps, s);
+            if (e != cudaSuccess) return cuda_fail(e, "octree deposit launch");
+        } else {
+            if (o.schedule == PSE_THREAD_PER_TET) e = pse::launch_thread_per_tet(q, o.precision == PSE_FP64_PLAIN, stats, s);
+            else if (binned) e = pse::launch_binned(q, stats, bps, s);
+            else e = pse::launch_warp_coop(q, stats, bps, s);
+            if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+        }
+        return PSE_OK;
+    };
     // the whole launch sequence of the call, on stream s
     auto enqueue = [&](cudaStream_t s) -> int {
         cudaError_t e = cudaMemsetAsync(p.ws, 0, pse::kWorkspaceBytes, s);
         if (e != cudaSuccess) return cuda_fail(e, "workspace clear");
-        if (qbits_len) {
+        if (qbits_len && !streamed) {
             e = cudaMemsetAsync(p.qbits, 0, qbits_len, s);
             if (e != cudaSuccess) return cuda_fail(e, "queue bitmap clear");
         }
@@ -216,16 +308,23 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
             e = cudaMemsetAsync(p.out, 0, (size_t)cells * sizeof(double), s);
             if (e != cudaSuccess) return cuda_fail(e, "output clear");
         }
-        if (p.n_units > 0 && p.leaves) {
-            e = pse::launch_octree_deposit(p, o.precision == PSE_FP64_PLAIN, o.schedule == PSE_THREAD_PER_TET, stats,
-                                           bps, s);
-            if (e != cudaSuccess) return cuda_fail(e, "octree deposit launch");
-        } else if (p.n_units > 0) {
-            if (o.schedule == PSE_THREAD_PER_TET) e = pse::launch_thread_per_tet(p, o.precision == PSE_FP64_PLAIN, stats, s);
-            else if (binned) e = pse::launch_binned(p, stats, bps, s);
-            else e = pse::launch_warp_coop(p, stats, bps, s);
-            if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
+        int r;
+        if (!streamed) {
+            r = launch(p, s);
+        } else {
+            // statistics and mass sums run over all slabs; the work counter and the binned
+            // schedule's queue state restart with every slab
+            r = stream_slabs(h_pos, p, slab_cubes, s, [&](pse::DepositParams &q, cudaStream_t ss) -> int {
+                cudaError_t e2 = cudaMemsetAsync(&q.ws->work_counter, 0, sizeof(q.ws->work_counter), ss);
+                if (e2 == cudaSuccess)
+                    e2 = cudaMemsetAsync(&q.ws->queue_count, 0,
+                                         sizeof(pse::Workspace) - offsetof(pse::Workspace, queue_count), ss);
+                if (e2 == cudaSuccess && qbits_len) e2 = cudaMemsetAsync(q.qbits, 0, qbits_len, ss);
+                if (e2 != cudaSuccess) return cuda_fail(e2, "slab workspace reset");
+                return launch(q, ss);
+            });
         }
+        if (r != PSE_OK) return r;
         if (renorm && p.n_units > 0) {
             e = pse::launch_scale(p.out, cells, p.ws, s);
             if (e != cudaSuccess) return cuda_fail(e, "mass renormalisation launch");
@@ -661,6 +760,114 @@ int pse_deposit_tets(const float *d_verts, const double *d_tet_mass, int64_t n_t
     fill_grid(p, grid_n, box);
     p.out = d_cell_mass;
     return run_deposit(p, o, cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// slab streaming from host memory
+// ---------------------------------------------------------------------------
+namespace {
+int check_streamed(const float *h_pos, const pse_lattice *lat, int64_t slab_cubes, const pse_deposit_opts &o)
+{
+    int rc = check_lattice(lat);
+    if (rc != PSE_OK) return rc;
+    if (!h_pos) return fail(PSE_ERR_INVALID_ARG, "h_pos is NULL");
+    if (!lat->periodic) return fail(PSE_ERR_UNSUPPORTED, "slab streaming needs a periodic lattice");
+    if (slab_cubes < 1) return fail(PSE_ERR_INVALID_ARG, "slab_cubes must be >= 1");
+    if (o.d_cube_ids) return fail(PSE_ERR_UNSUPPORTED, "slab streaming deposits whole lattices (d_cube_ids must be NULL)");
+    if (o.tuning && static_cast<const pse_tuning *>(o.tuning)->use_graph)
+        return fail(PSE_ERR_UNSUPPORTED, "slab streaming does not replay graphs (use_graph must be 0)");
+    return PSE_OK;
+}
+}  // namespace
+
+int pse_deposit_uniform_streamed(const float *h_pos, const pse_lattice *lat, int64_t slab_cubes,
+                                 const int64_t grid_n[3], double *d_cell_mass, const pse_deposit_opts *opts,
+                                 pse_deposit_stats *h_stats, void *d_ws, size_t ws_bytes, void *stream)
+{
+    g_last_error.clear();
+    const pse_deposit_opts o = opts ? *opts : default_opts();
+    int rc = check_opts(o);
+    if (rc != PSE_OK) return rc;
+    rc = check_streamed(h_pos, lat, slab_cubes, o);
+    if (rc != PSE_OK) return rc;
+    if (!d_cell_mass) return fail(PSE_ERR_INVALID_ARG, "d_cell_mass is NULL");
+    int64_t cells = 0;
+    rc = check_grid(grid_n, cells);
+    if (rc != PSE_OK) return rc;
+    pse::DepositParams p;
+    std::memset(&p, 0, sizeof(p));
+    lattice_params(p, h_pos, lat, o);
+    fill_grid(p, grid_n, lat->box);
+    p.out = d_cell_mass;
+    return run_deposit(p, o, cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream), h_pos, slab_cubes);
+}
+
+int pse_deposit_octree_streamed(const float *h_pos, const pse_lattice *lat, int64_t slab_cubes, const pse_octree *oct,
+                                double *d_leaf_mass, const pse_deposit_opts *opts, pse_deposit_stats *h_stats,
+                                void *d_ws, size_t ws_bytes, void *stream)
+{
+    g_last_error.clear();
+    const pse_deposit_opts o = opts ? *opts : default_opts();
+    int rc = check_opts(o);
+    if (rc != PSE_OK) return rc;
+    rc = check_streamed(h_pos, lat, slab_cubes, o);
+    if (rc != PSE_OK) return rc;
+    if (!oct || !d_leaf_mass) return fail(PSE_ERR_INVALID_ARG, "oct and d_leaf_mass must be non-NULL");
+    if (!oct->d_leaves || !oct->d_fine_map || oct->n_leaves < 1) return fail(PSE_ERR_INVALID_ARG, "oct is empty");
+    if (oct->box != lat->box) return fail(PSE_ERR_INVALID_ARG, "oct->box differs from lat->box");
+    pse::DepositParams p;
+    std::memset(&p, 0, sizeof(p));
+    lattice_params(p, h_pos, lat, o);
+    p.out = d_leaf_mass;
+    p.bc = oct->bc;
+    p.max_level = oct->max_level;
+    p.leaves = oct->d_leaves;
+    p.fine_map = oct->d_fine_map;
+    p.fine = (int64_t)1 << oct->max_level;
+    return run_deposit(p, o, oct->n_cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream), h_pos,
+                       slab_cubes);
+}
+
+int pse_build_octree_streamed(const float *h_pos, const pse_lattice *lat, int64_t slab_cubes, int32_t bc,
+                              int32_t max_level, double edge_threshold_cells, pse_octree *out, void *stream)
+{
+    g_last_error.clear();
+    const pse_deposit_opts o = default_opts();
+    int rc = check_streamed(h_pos, lat, slab_cubes, o);
+    if (rc != PSE_OK) return rc;
+    if (!out) return fail(PSE_ERR_INVALID_ARG, "out is NULL");
+    if (bc < 1 || bc > 4096) return fail(PSE_ERR_INVALID_ARG, "bc = %d out of range [1, 4096]", bc);
+    if (max_level < 0 || max_level > kMaxOctreeLevel) return fail(PSE_ERR_INVALID_ARG, "max_level out of range");
+    if (!(edge_threshold_cells > 0.0)) return fail(PSE_ERR_INVALID_ARG, "edge_threshold_cells must be > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t hb = hist_bytes(max_level);
+    std::vector<unsigned> hist(hb / sizeof(unsigned), 0u);
+    if (max_level > 0) {
+        unsigned *d_hist = nullptr;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_hist), hb, st);
+        if (e != cudaSuccess) return fail(PSE_ERR_OOM, "histogram allocation failed: %s", cudaGetErrorString(e));
+        e = cudaMemsetAsync(d_hist, 0, hb, st);
+        pse::DepositParams p;
+        std::memset(&p, 0, sizeof(p));
+        lattice_params(p, h_pos, lat, o);
+        p.bc = bc;
+        p.max_level = max_level;
+        if (e == cudaSuccess) {
+            // the histograms accumulate over the slabs
+            rc = stream_slabs(h_pos, p, slab_cubes, st, [&](pse::DepositParams &q, cudaStream_t ss) -> int {
+                cudaError_t e2 = pse::launch_octree_hist(q, d_hist, ss);
+                return e2 == cudaSuccess ? PSE_OK : cuda_fail(e2, "histogram launch");
+            });
+        }
+        if (e == cudaSuccess && rc == PSE_OK) e = cudaMemcpyAsync(hist.data(), d_hist, hb, cudaMemcpyDeviceToHost, st);
+        cudaFreeAsync(d_hist, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (rc != PSE_OK) return rc;
+        if (e != cudaSuccess) return cuda_fail(e, "octree histograms");
+    }
+    std::vector<int32_t> leaves;
+    decide(hist, max_level, edge_threshold_cells, 0, 0, 0, 0, leaves);
+    return make_octree(leaves.data(), (int64_t)(leaves.size() / 4), bc, max_level, lat->box, out);
 }
 
 // ---------------------------------------------------------------------------

@@ -69,7 +69,11 @@ __device__ __forceinline__ void lattice_tet(const DepositParams &P, int64_t ci, 
         if (q == 1) { i += o1[0]; j += o1[1]; k += o1[2]; }
         if (q == 2) { i += o2[0]; j += o2[1]; k += o2[2]; }
         if (q == 3) { i += 1; j += 1; k += 1; }
-        if (P.periodic) { i = wrap_idx(i, P.n[0]); j = wrap_idx(j, P.n[1]); k = wrap_idx(k, P.n[2]); }
+        if (P.periodic) {
+            i = wrap_idx(i, P.n[0]);
+            j = wrap_idx(j, P.n[1]);
+            if (!P.slab) k = wrap_idx(k, P.n[2]);
+        }
         const float *p = P.pos + 3 * (i + P.n[0] * (j + P.n[1] * k));
         x[q][0] = __ldg(p);
         x[q][1] = __ldg(p + 1);

@@ -163,8 +163,10 @@ __device__ __forceinline__ int chunk_setup(const DepositParams &P, WarpSmem *S, 
     return len;
 }
 
+constexpr int kCoopThreads = 128;
+
 template <bool STATS, int MINB, bool BINNED>
-__global__ void __launch_bounds__(256, MINB) k_warp_coop(const DepositParams P)
+__global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
@@ -482,15 +484,20 @@ namespace {
 template <bool BINNED>
 cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, int64_t max_items, cudaStream_t st)
 {
-    const int threads = 256;
+    // blocks_per_sm resident blocks of 128 threads: 2 (255 registers per thread, 8 warps per
+    // SM), 3 (170 registers, 12 warps) or 4 (128 registers, 16 warps).  The counting
+    // variant (stats) is built for 2 only.
+    const int threads = kCoopThreads;
     const size_t smem = sizeof(WarpSmem) * (threads / 32);
-    const int minb = (blocks_per_sm >= 2) ? 2 : 1;
-    const void *k = stats ? (minb == 2 ? (const void *)k_warp_coop<true, 2, BINNED> : (const void *)k_warp_coop<true, 1, BINNED>)
-                          : (minb == 2 ? (const void *)k_warp_coop<false, 2, BINNED> : (const void *)k_warp_coop<false, 1, BINNED>);
+    const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
+    const void *k = stats ? (const void *)k_warp_coop<true, 2, BINNED>
+                    : minb == 4 ? (const void *)k_warp_coop<false, 4, BINNED>
+                    : minb == 3 ? (const void *)k_warp_coop<false, 3, BINNED>
+                                : (const void *)k_warp_coop<false, 2, BINNED>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);
-    const int64_t need = (max_items + 7) / 8;
+    const int64_t need = (max_items + threads / 32 - 1) / (threads / 32);
     if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
     void *args[] = {const_cast<DepositParams *>(&p)};
     return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);

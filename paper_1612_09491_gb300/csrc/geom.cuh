@@ -89,6 +89,14 @@ PSE_HD double fdiv(double a, double b) { return a / b; }
 PSE_HD float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 PSE_HD double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
+// unit roundoff of each arithmetic type (the classification tolerance is a few of these)
+template <class T>
+PSE_HD T roundoff();
+template <>
+PSE_HD float roundoff<float>() { return 1.1920928955078125e-07f; }  // 2^-23
+template <>
+PSE_HD double roundoff<double>() { return 2.220446049250313e-16; }  // 2^-52
+
 // products rounded on their own (never fused), so that cross_xy(u, u) is exactly 0
 PSE_HD float mul_rn(float a, float b)
 {
@@ -178,7 +186,7 @@ PSE_HD P3<T> at_plane(const P3<T> &a, const P3<T> &b, T t, int ax, T s)
 
 // Clip slots [0, NE) against lo <= c_ax < hi; new edges go to slots NE (on lo) and NE+1 (on hi).
 template <class T, int NE>
-PSE_HD void clip_slab(P3<T> (&A)[9], P3<T> (&B)[9], int ax, T lo, T hi, T tol)
+PSE_HD void clip_slab(P3<T> (&A)[7], P3<T> (&B)[7], int ax, T lo, T hi, T tol)
 {
     const P3<T> z0 = mk<T>(T(0), T(0), T(0));
     P3<T> xl = z0, nl = z0, xh = z0, nh = z0;  // exit / entry points on lo and on hi
@@ -218,15 +226,27 @@ PSE_HD T fan_const(const P3<T> &a, const P3<T> &b, T s, T l0, T lx, T ly)
     return cross_xy(a, b) * ((s - l0) + fa + fb);
 }
 
-// Split slots [0, NE) at z = lo and z = hi: the part in between stays (new edges in slots
-// NE, NE+1); the parts below and above are integrated on the fly (fan from the local
-// origin, integrands lo - l and hi - l).  Returns 6 * their integral.
+// 6 * integral of (z - l(x,y)) over the projection of the fan triangle (o, a, b)
+template <class T>
+PSE_HD T fan_mid(const P3<T> &a, const P3<T> &b, const P3<T> &o, T fo, T l0, T lx, T ly)
+{
+    const T fa = a.z - fmaT(lx, a.x, fmaT(ly, a.y, l0));
+    const T fb = b.z - fmaT(lx, b.x, fmaT(ly, b.y, l0));
+    return cross_xy(sub(a, o), sub(b, o)) * (fo + fa + fb);
+}
+
+// Split slots [0, NE) at z = lo and z = hi and integrate all three parts in one pass:
+// below lo and above hi the integrands are lo - l and hi - l (fans from the local
+// origin); in between it is z - l (fan from o, a point of the face plane).  Returns
+// 6 * the whole integral; mag accumulates the magnitudes of the three parts.
 template <class T, int NE>
-PSE_HD T split_zslab(P3<T> (&A)[9], P3<T> (&B)[9], T lo, T hi, T tol, T l0, T lx, T ly, T &mag)
+PSE_HD T split_zslab(const P3<T> (&A)[7], const P3<T> (&B)[7], T lo, T hi, T tol, T l0, T lx, T ly,
+                     const P3<T> &o, T &mag)
 {
     const P3<T> z0 = mk<T>(T(0), T(0), T(0));
     P3<T> xl = z0, nl = z0, xh = z0, nh = z0;
-    T below = T(0), above = T(0);
+    T below = T(0), above = T(0), mid = T(0);
+    const T fo = o.z - fmaT(lx, o.x, fmaT(ly, o.y, l0));
 #pragma unroll
     for (int k = 0; k < NE; ++k) {
         const P3<T> a = A[k], b = B[k];
@@ -240,25 +260,23 @@ PSE_HD T split_zslab(P3<T> (&A)[9], P3<T> (&B)[9], T lo, T hi, T tol, T l0, T lx
         below += (a_lo || b_lo) ? fan_const(ba, bb, lo, l0, lx, ly) : T(0);
         const P3<T> ua = a_hi ? a : ph, ub = b_hi ? b : ph;
         above += (a_hi || b_hi) ? fan_const(ua, ub, hi, l0, lx, ly) : T(0);
+        // the part in between
         const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
-        P3<T> na = a_lo ? pl : (a_hi ? ph : a);
-        P3<T> nb = b_lo ? pl : (b_hi ? ph : b);
-        A[k] = drop ? z0 : na;
-        B[k] = drop ? z0 : nb;
+        const P3<T> na = a_lo ? pl : (a_hi ? ph : a);
+        const P3<T> nb = b_lo ? pl : (b_hi ? ph : b);
+        mid += drop ? T(0) : fan_mid(na, nb, o, fo, l0, lx, ly);
         xl = (!a_lo && b_lo) ? pl : xl;
         nl = (a_lo && !b_lo) ? pl : nl;
         xh = (!a_hi && b_hi) ? ph : xh;
         nh = (a_hi && !b_hi) ? ph : nh;
     }
-    A[NE] = xl;
-    B[NE] = nl;
-    A[NE + 1] = xh;
-    B[NE + 1] = nh;
-    // closing edges of the parts below (entry -> exit on lo) and above (on hi)
+    // closing edges: of the part below (entry -> exit on lo), above (on hi), and of the
+    // part in between (exit -> entry on each plane)
     below += fan_const(nl, xl, lo, l0, lx, ly);
     above += fan_const(nh, xh, hi, l0, lx, ly);
-    mag += fabs(below) + fabs(above);
-    return below + above;
+    mid += fan_mid(xl, nl, o, fo, l0, lx, ly) + fan_mid(xh, nh, o, fo, l0, lx, ly);
+    mag += fabs(below) + fabs(above) + fabs(mid);
+    return below + above + mid;
 }
 
 // ---------------------------------------------------------------------------
@@ -302,30 +320,19 @@ PSE_HD T overlap_volume(const P3<T> (&p)[4], const P3<T> (&n)[4], T lx, T ly, T 
         // classification tolerance: a few units of rounding of this face's coordinates
         const T cmag = fmax(T(1), fmax(fmax(fmax(fabs(mnx), fabs(mxx)), fmax(fabs(mny), fabs(mxy))),
                                        fmax(fabs(mnz), fabs(mxz))));
-        const T tol = T(8) * (sizeof(T) == 4 ? T(1.1920928955078125e-07) : T(2.220446049250313e-16)) * cmag;  // 8 ulp(1) x cmag
+        const T tol = T(8) * roundoff<T>() * cmag;
         // anchor of the between-planes region: the local origin projected onto the face plane
         const T sc = fdiv(dot(nf, a), dot(nf, nf));
         const P3<T> o = mk<T>(sc * nf.x, sc * nf.y, sc * nf.z);
 
-        P3<T> A[9], B[9];
+        P3<T> A[7], B[7];
         A[0] = a; B[0] = b;
         A[1] = b; B[1] = c;
         A[2] = c; B[2] = a;
         A[3] = B[3] = A[4] = B[4] = mk<T>(T(0), T(0), T(0));
         clip_slab<T, 3>(A, B, 0, xlo, xhi, tol);
         clip_slab<T, 5>(A, B, 1, ylo, yhi, tol);
-        T outside = split_zslab<T, 7>(A, B, zlo, zhi, tol, l0, lx, ly, mag);
-        // between the planes: integrand z - l, fan from o
-        const T fo = o.z - fmaT(lx, o.x, fmaT(ly, o.y, l0));
-        T mid = T(0);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const T fa = A[k].z - fmaT(lx, A[k].x, fmaT(ly, A[k].y, l0));
-            const T fb = B[k].z - fmaT(lx, B[k].x, fmaT(ly, B[k].y, l0));
-            mid = fmaT(cross_xy(sub(A[k], o), sub(B[k], o)), fo + fa + fb, mid);
-        }
-        vol += outside + mid;
-        mag += fabs(mid);
+        vol += split_zslab<T, 7>(A, B, zlo, zhi, tol, l0, lx, ly, o, mag);
     }
     err = mag * T(1.0 / 6.0);
     return vol * T(1.0 / 6.0);

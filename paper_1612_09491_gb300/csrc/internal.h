@@ -46,7 +46,9 @@ struct DepositParams {
     int32_t src;
     int32_t periodic;
     const float *pos;          // SRC_LATTICE / SRC_CUBE_LIST: float32 [n0*n1*n2][3]
-    int64_t n[3];              // particles per axis
+    int64_t n[3];              // particles per axis (slab mode: n[2] = rows held in pos)
+    int32_t slab;              // 1: pos holds the particle rows of a z-slab plus one halo row; z
+                               //    indices are slab-local and never wrapped (x, y still are)
     int64_t nc[3];             // cubes per axis (n for periodic, n-1 for open)
     const int64_t *cube_ids;   // SRC_CUBE_LIST
     const float *verts;        // SRC_TETS: float32 [n_tets][4][3]

@@ -29,7 +29,11 @@ __device__ __forceinline__ void lattice_tet_raw(const DepositParams &P, int64_t 
         if (q == 1) { i += o1[0]; j += o1[1]; kk += o1[2]; }
         if (q == 2) { i += o2[0]; j += o2[1]; kk += o2[2]; }
         if (q == 3) { i += 1; j += 1; kk += 1; }
-        if (P.periodic) { i = wrap_idx(i, P.n[0]); j = wrap_idx(j, P.n[1]); kk = wrap_idx(kk, P.n[2]); }
+        if (P.periodic) {
+            i = wrap_idx(i, P.n[0]);
+            j = wrap_idx(j, P.n[1]);
+            if (!P.slab) kk = wrap_idx(kk, P.n[2]);
+        }
         const float *p = P.pos + 3 * (i + P.n[0] * (j + P.n[1] * kk));
         x[q][0] = __ldg(p);
         x[q][1] = __ldg(p + 1);
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
 // warp-cooperative FP32 path: per sub-batch, rounds of (tetrahedron, leaf) pairs
 // ---------------------------------------------------------------------------
 template <bool STATS, int MINB>
-__global__ void __launch_bounds__(256, MINB) k_oct_warp(const DepositParams P)
+__global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
@@ -545,15 +549,19 @@ cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread
         void *args[] = {const_cast<DepositParams *>(&p)};
         return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(threads), args, 0, st);
     }
-    const int threads = 256;
+    // blocks_per_sm resident blocks of 128 threads: 2 (255 registers), 3 (170) or 4 (128);
+    // the counting variant (stats) is built for 2 only
+    const int threads = 128;
     const size_t smem = sizeof(WarpSmem) * (threads / 32);
-    const int minb = (blocks_per_sm >= 2) ? 2 : 1;
-    const void *k = stats ? (minb == 2 ? (const void *)k_oct_warp<true, 2> : (const void *)k_oct_warp<true, 1>)
-                          : (minb == 2 ? (const void *)k_oct_warp<false, 2> : (const void *)k_oct_warp<false, 1>);
+    const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
+    const void *k = stats ? (const void *)k_oct_warp<true, 2>
+                    : minb == 4 ? (const void *)k_oct_warp<false, 4>
+                    : minb == 3 ? (const void *)k_oct_warp<false, 3>
+                                : (const void *)k_oct_warp<false, 2>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);
-    const int64_t need = (p.n_items + 7) / 8;
+    const int64_t need = (p.n_items + 3) / 4;
     if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
     void *args[] = {const_cast<DepositParams *>(&p)};
     return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);

@@ -12,4 +12,5 @@ from .lattice import (  # noqa: F401
     lattice_positions,
     random_dyadic_tets,
     zeldovich_positions,
+    zeldovich_positions_device,
 )

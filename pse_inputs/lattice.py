@@ -153,3 +153,50 @@ def random_dyadic_tets(count: int, seed: int, span: float = 3.0, denom_bits: int
             out[i] = v
             i += 1
     return out
+
+
+def zeldovich_positions_device(n: int, spectral_index: float, rms_disp: float, seed: int, box: float = 1.0,
+                               device="cuda", out=None):
+    """The Zel'dovich recipe above for the large lattices (512^3, 1024^3), evaluated on the GPU with
+    torch.fft in float32: white noise from torch's generator seeded with `seed` (not numpy's, so the
+    field differs from zeldovich_positions at the same seed), one displacement component at a time.
+    Returns float32 [n^3, 3] on `device` (or fills `out`, which may live in host memory)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    w = torch.randn((n, n, n), generator=g, device=device, dtype=torch.float32)  # axes (z, y, x)
+    wk = torch.fft.rfftn(w)
+    del w
+    kz = torch.fft.fftfreq(n, d=1.0 / n, device=device).view(n, 1, 1)
+    ky = torch.fft.fftfreq(n, d=1.0 / n, device=device).view(1, n, 1)
+    kx = torch.fft.rfftfreq(n, d=1.0 / n, device=device).view(1, 1, n // 2 + 1)
+    k2 = kx * kx + ky * ky + kz * kz
+    k2[0, 0, 0] = 1.0
+    amp = torch.pow(k2, 0.25 * spectral_index)  # sqrt(P(k)), P = k^index
+    nyq = n // 2
+    kill = (kx.abs() == nyq) | (ky.abs() == nyq) | (kz.abs() == nyq)
+    wk *= amp
+    wk[0, 0, 0] = 0.0
+    wk = torch.where(kill, torch.zeros((), dtype=wk.dtype, device=device), wk)
+    del amp, kill
+    if out is None:
+        out = torch.empty((n ** 3, 3), dtype=torch.float32, device=device)
+    ms = 0.0
+    q = (torch.arange(n, device=device, dtype=torch.float64) * (box / n))
+    comps = []
+    for a, ka in enumerate((kx, ky, kz)):
+        c = torch.fft.irfftn(wk * (1j * ka / k2), s=(n, n, n))
+        ms += float((c.double() ** 2).sum()) / n ** 3
+        comps.append(c)
+        del c
+    scale = (rms_disp * box / n) / max(ms, 1e-300) ** 0.5
+    for a in range(3):
+        shape = [1, 1, 1]
+        shape[2 - a] = n
+        x = comps[a].double() * scale + q.view(*shape)
+        x = torch.remainder(x, box).float()
+        x[x >= box] = 0.0
+        out[:, a].copy_(x.reshape(-1))
+        comps[a] = None
+        del x
+    return out
