@@ -42,6 +42,12 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 FLOP_PER_TET = 150.0
 FLOP_PER_BBOX_CELL = 32.0
 FLOP_PER_CLIP = 620.0
+# From one ncu capture of the tuned deposit kernel (k_warp_coop, 3 blocks of 128 threads
+# per SM) on the headline workload: DRAM bytes read + written per launch, and thread
+# instructions issued per partial clip (warp instructions x active lanes / partial clips).
+# Both go stale when the kernel changes and must be re-taken with it.
+DRAM_BYTES_PER_LAUNCH = 259_667_968
+THREAD_INST_PER_CLIP = 4812.0
 SM_COUNT_GB300 = 152
 PRECISION = "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up"
 FP32_LANES_PER_SM = 128
@@ -541,8 +547,17 @@ def main():
             "error_vs_oracle": oracle_err,
             "kernel_ms": kern_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": DRAM_BYTES_PER_LAUNCH if tuned == {"blocks_per_sm": 3, "schedule": "warp"}
+                         else None, "traffic_unit": "bytes per launch (ncu dram read + write)",
                          "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"},
+            "issue": {"thread_inst_per_clip": THREAD_INST_PER_CLIP,
+                      "achieved_tinst_per_s": THREAD_INST_PER_CLIP * st["partial_clips"] / (kern_ms * 1e-3),
+                      "peak_tinst_per_s": sms * 4 * 32 * max_mhz * 1e6,
+                      "frac": THREAD_INST_PER_CLIP * st["partial_clips"] / (kern_ms * 1e-3) /
+                              (sms * 4 * 32 * max_mhz * 1e6),
+                      "note": "instruction issue of the deposit kernel against one warp instruction per "
+                              "scheduler per clock (4 per SM), all 32 lanes"},
             "cpu_baseline": cpu,
             "e2e": {"value": world * n_tets / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(pos_host.nbytes),
                     "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": e2e_ms},
