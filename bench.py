@@ -193,6 +193,22 @@ def run_reference(args, cfg):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- replicas ----
+def replica_throughput(step_ms, units_per_rank, dist=None, device="cpu"):
+    """Whole-job throughput of N independent replicas: every rank processed units_per_rank
+    per step; the step time is the slowest rank's mean (max over ranks).
+    Returns (ms_per_step, units per second over all ranks)."""
+    import torch
+    ms = sum(step_ms) / len(step_ms)
+    world = 1
+    if dist is not None:
+        world = dist.get_world_size()
+        t = torch.tensor([ms], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 # ---------------------------------------------------------- other workloads --
 def _timed(step, steps, warmup, flush, stream):
     """CUDA-event times (ms) of `steps` calls of step() after `warmup` untimed ones, L2 flushed between."""
@@ -459,12 +475,7 @@ def main():
         t_wall = time.perf_counter() - t_wall0
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = sum(step_ms) / len(step_ms)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_tets / (ms * 1e-3)
+    ms, value = replica_throughput(step_ms, n_tets, dist, dev)
     clips_per_s = world * st["partial_clips"] / (ms * 1e-3)
 
     # kernel-only duration (accumulate mode: no output clear), for the roofline
