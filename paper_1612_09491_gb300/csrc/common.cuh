@@ -284,7 +284,8 @@ struct WarpSmem {
     float e[4][32];
     float pos[4][32];
     float neg[4][32];
-    float lx[32], ly[32];  // reference-plane slopes
+    float lx[32], ly[32];  // reference-plane slopes (in the clip's frame)
+    int axis[32];          // the clip's divergence axis (to_axis)
     int lo[3][32];
     int dim[3][32];
     int base[3][32];
@@ -370,6 +371,7 @@ __device__ __forceinline__ void store_record(WarpSmem *S, int lane, const TetSet
     S->rho[lane] = 6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6);
     S->lx[lane] = ts.lx;
     S->ly[lane] = ts.ly;
+    S->axis[lane] = ts.axis;
     S->guard[lane] = guard;
     S->skip[lane] = skip;
     if (guard) store_residuals(S, lane, res);
@@ -412,7 +414,7 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
 #pragma unroll
             for (int f = 0; f < 4; ++f) n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
             float err;
-            vol = (double)overlap_volume<float>(p, n, S->lx[t], S->ly[t], err);
+            vol = (double)overlap_volume_ax<float>(p, n, S->axis[t], S->lx[t], S->ly[t], err);
         } else {
             vol = redo_fp64(S, t, cx, cy, cz);
             if (STATS) cnt.u[ST_FP64_REDOS]++;

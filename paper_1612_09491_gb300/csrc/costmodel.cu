@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(128) k_tet_counts(const DepositParams P, int32
                                     for (int q = 0; q < 4; ++q)
                                         p[q] = mk<float>(ts.v[q].x - cx, ts.v[q].y - cy, ts.v[q].z - cz);
                                     float err;
-                                    vol = (double)overlap_volume<float>(p, ts.n, ts.lx, ts.ly, err);
+                                    vol = (double)overlap_volume_ax<float>(p, ts.n, ts.axis, ts.lx, ts.ly, err);
                                 }
                                 if (vol > kOverlapFloor) ++n_ov;
                             }

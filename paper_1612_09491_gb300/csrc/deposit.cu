@@ -101,11 +101,11 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                                 if (STATS) cnt.u[ST_FP64_REDOS]++;
                             } else {
                                 T err;
-                                vol = (double)overlap_volume<T>(p, ts.n, ts.lx, ts.ly, err);
+                                vol = (double)overlap_volume_ax<T>(p, ts.n, ts.axis, ts.lx, ts.ly, err);
                             }
                         } else {
                             T err;
-                            vol = (double)overlap_volume<T>(p, ts.n, ts.lx, ts.ly, err);
+                            vol = (double)overlap_volume_ax<T>(p, ts.n, ts.axis, ts.lx, ts.ly, err);
                         }
                         if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
                     }

@@ -338,6 +338,30 @@ PSE_HD T overlap_volume(const P3<T> (&p)[4], const P3<T> (&n)[4], T lx, T ly, T 
     return vol * T(1.0 / 6.0);
 }
 
+// Cyclic relabelling of the axes that brings `axis` to z (orientation preserving).
+template <class T>
+PSE_HD P3<T> to_axis(const P3<T> &a, int axis)
+{
+    P3<T> r = a;
+    r = (axis == 0) ? mk<T>(a.y, a.z, a.x) : r;
+    r = (axis == 1) ? mk<T>(a.z, a.x, a.y) : r;
+    return r;
+}
+
+// The clip in the frame where the tetrahedron's largest face is the most horizontal one:
+// p, n as for overlap_volume; lx, ly: reference slopes in that frame (tet_setup).
+template <class T>
+PSE_HD T overlap_volume_ax(const P3<T> (&p)[4], const P3<T> (&n)[4], int axis, T lx, T ly, T &err)
+{
+    P3<T> pa[4], na[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        pa[q] = to_axis(p[q], axis);
+        na[q] = to_axis(n[q], axis);
+    }
+    return overlap_volume<T>(pa, na, lx, ly, err);
+}
+
 // Slopes of the reference plane l: the plane of the face whose normal is closest to
 // the z axis, unless that plane is steeper than 8 (then l is horizontal).
 template <class T>
@@ -416,7 +440,8 @@ struct TetSetup {
     int lo[3], dim[3]; // bounding-box cells relative to the base: [lo, lo + dim)
     double vol6;       // |6 V| in grid units (float64)
     float kappa;       // conditioning estimate (surface * extent / volume)
-    T lx, ly;          // slopes of the reference plane l (the most horizontal face's plane)
+    int axis;          // the clip integrates along this axis (the largest face's dominant normal axis)
+    T lx, ly;          // slopes of the reference plane l in the clip's frame (to_axis)
 };
 
 // Returns true if v[1] and v[2] were swapped to make the tetrahedron positively oriented.
@@ -481,7 +506,26 @@ PSE_HD bool tet_setup(P3<T> (&v)[4], TetSetup<T> &s)
         s.lo[a] = lo[a];
         s.dim[a] = hi[a] - lo[a] + 1;
     }
-    ref_slopes<T>(s.n, s.lx, s.ly);
+    // divergence axis: the dominant component of the largest face's normal, so that this
+    // face (and, for a sliver, its near-parallel partner) is close to horizontal in the
+    // clip's frame; thin dimensions are then integrated along the axis, not across it
+    {
+        int fb = 0;
+        T best = T(-1);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const T a2 = dot(s.n[f], s.n[f]);
+            fb = (a2 > best) ? f : fb;
+            best = (a2 > best) ? a2 : best;
+        }
+        const P3<T> nb = pick4(s.n, fb);
+        const T ax = fabs(nb.x), ay = fabs(nb.y), az = fabs(nb.z);
+        s.axis = (az >= ax && az >= ay) ? 2 : (ax >= ay ? 0 : 1);
+        P3<T> na[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) na[f] = to_axis(s.n[f], s.axis);
+        ref_slopes<T>(na, s.lx, s.ly);
+    }
     const double denom = s.vol6 > 0.0 ? s.vol6 : 1e-300;
     s.kappa = (float)((double)area2 * sqrt((double)lmax2) / denom);
     return d6 < 0.0;

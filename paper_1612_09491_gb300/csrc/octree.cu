@@ -297,11 +297,11 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
                                         if (STATS) cnt.u[ST_FP64_REDOS]++;
                                     } else {
                                         T err;
-                                        vol = (double)overlap_volume<T>(p, ts.n, ts.lx, ts.ly, err);
+                                        vol = (double)overlap_volume_ax<T>(p, ts.n, ts.axis, ts.lx, ts.ly, err);
                                     }
                                 } else {
                                     T err;
-                                    vol = (double)overlap_volume<T>(p, ts.n, ts.lx, ts.ly, err);
+                                    vol = (double)overlap_volume_ax<T>(p, ts.n, ts.axis, ts.lx, ts.ly, err);
                                 }
                                 if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
                             }
@@ -439,6 +439,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                 S->rho[lane] = 6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6);
                                 S->lx[lane] = ts.lx;
                                 S->ly[lane] = ts.ly;
+                                S->axis[lane] = ts.axis;
                                 S->guard[lane] = guard;
                                 S->skip[lane] = 0;
                                 if (guard) store_residuals(S, lane, res);
