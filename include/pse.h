@@ -152,7 +152,7 @@ typedef struct pse_tuning {
     int32_t split_cells;     /* binned schedule: a tetrahedron whose bounding box has more cells than
                                 this is split across warps; <= 0: default 1024 */
     int32_t chunk_cells;     /* binned schedule: bounding-box cells per split work item; <= 0: default 512 */
-    int32_t use_graph;       /* binned schedule with a caller workspace: 1 = replay the call's launch
+    int32_t use_graph;       /* with a caller workspace and h_stats NULL: 1 = replay the call's launch
                                 sequence as a CUDA graph (captured once per distinct argument set) */
     int32_t reserved[5];
 } pse_tuning;

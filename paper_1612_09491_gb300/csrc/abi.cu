@@ -246,7 +246,7 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
     const pse_tuning *tu = static_cast<const pse_tuning *>(o.tuning);
     const bool stats = h_stats != nullptr;
     const bool streamed = h_pos != nullptr;
-    const bool graph = binned && tu && tu->use_graph && d_ws != nullptr && !stats && !streamed;
+    const bool graph = tu && tu->use_graph && d_ws != nullptr && !stats && !streamed;
     WsLease lease;
     // streamed: tetrahedron ids (cost-model bitmap) are slab-local
     const int64_t n_tets = streamed ? 6 * p.nc[0] * p.nc[1] * std::min(slab_cubes, p.nc[2])

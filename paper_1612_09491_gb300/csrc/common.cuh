@@ -291,7 +291,7 @@ struct WarpSmem {
     int base[3][32];
     int leaf[32];         // octree: leaf of this (tetrahedron, leaf) pair
     int org[3][32];       // octree: the leaf's first cell, base-cell frame
-    double rho[32];
+    float rho[32];        // 6 m_t / |6V| (deposit = rho * overlap volume, formed in float32)
     int start[32];        // exclusive prefix of the pair counts
     int skip[32];         // first bounding-box cell of this record (split tetrahedra; else 0)
     int guard[32];        // 1: clip this tetrahedron in float64
@@ -368,7 +368,7 @@ __device__ __forceinline__ void store_record(WarpSmem *S, int lane, const TetSet
         S->base[a][lane] = base[a];
     }
     const int guard = (ts.kappa <= kappa_max) ? 0 : 1;
-    S->rho[lane] = 6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6);
+    S->rho[lane] = (float)(6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6));
     S->lx[lane] = ts.lx;
     S->ly[lane] = ts.ly;
     S->axis[lane] = ts.axis;
@@ -421,7 +421,7 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
         }
         if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
         if (vol > 0.0) {
-            const double m = S->rho[t] * vol;
+            const double m = (double)(S->rho[t] * (float)vol);
             cnt.dep += m;
             if (!deposit_pair<OCT>(P, S, t, cx, cy, cz, m) && STATS) cnt.dropped += m;
         }
@@ -473,7 +473,7 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                 }
                 const int cls = classify_cell<float>(n, e, ps, ng, cx, cy, cz);
                 if (cls == CELL_INSIDE) {
-                    const double m = S->rho[t];
+                    const double m = (double)S->rho[t];
                     cnt.dep += m;
                     if (!deposit_pair<OCT>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) && STATS)
                         cnt.dropped += m;

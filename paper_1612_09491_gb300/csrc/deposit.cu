@@ -231,20 +231,20 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                 npairs = chunk_setup<STATS>(P, S, lane, (int64_t)item, q, cnt);
                 __syncwarp();
             } else if (unit >= 0) {
-                P3<float> v[4], res[4];
+                P3<float> v[4];
                 int base[3];
                 // tetrahedron id as the bin pass numbers it
                 const int64_t tid = (P.src == SRC_TETS) ? unit
                                     : 6 * ((P.src == SRC_LATTICE) ? ci + P.nc[0] * (cj + P.nc[1] * ck) : unit) + s;
                 if (P.src == SRC_TETS) {
-                    explicit_tet<float>(P, unit, v, base, res);
+                    explicit_tet<float>(P, unit, v, base);
                     m_t = P.tet_mass[unit];
                 } else {
-                    lattice_tet<float>(P, ci, cj, ck, s, v, base, res);
+                    lattice_tet<float>(P, ci, cj, ck, s, v, base);
                     m_t = P.m_tet;
                 }
                 TetSetup<float> ts;
-                if (tet_setup<float>(v, ts)) swap12(res);
+                const bool swapped = tet_setup<float>(v, ts);
                 if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
                 const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
                 if (!tet_ok(base, ts)) {
@@ -277,6 +277,17 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                     npairs = (int)ncell;
                     cnt.tgt += m_t;
                     if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
+                    // the vertices' rounding residuals, needed only by guarded tetrahedra
+                    P3<float> res[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) res[q] = mk<float>(0.f, 0.f, 0.f);
+                    if (!(ts.kappa <= P.kappa_max)) {
+                        P3<float> v2[4];
+                        int b2[3];
+                        if (P.src == SRC_TETS) explicit_tet<float>(P, unit, v2, b2, res);
+                        else lattice_tet<float>(P, ci, cj, ck, s, v2, b2, res);
+                        if (swapped) swap12(res);
+                    }
                     store_record(S, lane, ts, res, base, m_t, P.kappa_max, 0);
                 }
             }

@@ -386,9 +386,17 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                     if (more) {
                         P3<float> v[4], res[4];
                         int base[3];
-                        to_grid<float>(P, x, k, bc << hit.level, v, base, res);
+                        to_grid<float>(P, x, k, bc << hit.level, v, base);
                         TetSetup<float> ts;
-                        if (tet_setup<float>(v, ts)) swap12(res);
+                        const bool swapped = tet_setup<float>(v, ts);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) res[q] = mk<float>(0.f, 0.f, 0.f);
+                        if (!(ts.kappa <= P.kappa_max)) {  // rounding residuals for the guarded clip
+                            P3<float> v2[4];
+                            int b2[3];
+                            to_grid<float>(P, x, k, bc << hit.level, v2, b2, res);
+                            if (swapped) swap12(res);
+                        }
                         if (!tet_ok(base, ts)) {
                             set_error(P.ws, 4, lane);
                             more = false;
@@ -436,7 +444,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                 }
                                 S->leaf[lane] = hit.leaf;
                                 const int guard = (ts.kappa <= P.kappa_max) ? 0 : 1;
-                                S->rho[lane] = 6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6);
+                                S->rho[lane] = (float)(6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6));
                                 S->lx[lane] = ts.lx;
                                 S->ly[lane] = ts.ly;
                                 S->axis[lane] = ts.axis;

@@ -177,3 +177,19 @@ def test_config3_full_size_sampled():
     e = cell_errors(full, full64)
     assert e["max_rel"] <= 1e-5, e
     assert e["mass"] <= 1e-12, e
+
+
+def test_octree_graph_replay():
+    """use_graph on the octree deposit: replays equal plain calls, also after the positions change."""
+    n, bc, ml = 16, 4, 4
+    pos = torch.from_numpy(squeezed_lattice(n, seed=7)).cuda()
+    oct_ = pse.build_octree_from_tet_sizes(pos, n, bc, ml, 2.0)
+    ws = torch.empty(pse.workspace_size(pse._lib.PSE_OP_DEPOSIT_OCTREE), dtype=torch.uint8, device="cuda")
+    out = torch.empty((oct_.n_leaves, bc, bc, bc), dtype=torch.float64, device="cuda")
+    for seed in (7, 8):
+        pos.copy_(torch.from_numpy(squeezed_lattice(n, seed=seed)))
+        ref = pse.deposit_octree(pos, n, oct_).cpu().numpy()
+        for _ in range(2):
+            pse.deposit_octree(pos, n, oct_, out=out, workspace=ws, tuning={"use_graph": 1})
+            e = cell_errors(out.cpu().numpy(), ref)
+            assert e["max_rel"] <= 2e-6 and e["mass"] <= 1e-13, e

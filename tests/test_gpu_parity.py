@@ -158,9 +158,11 @@ def test_cell_inside_tet(name, prec, sched):
     g = 16
     tet = f32([[[0.05, 0.05, 0.05], [0.95, 0.1, 0.08], [0.1, 0.9, 0.1], [0.12, 0.11, 0.93]]])
     ref, _ = oracle.deposit_tets(tet, [1.0], g)
-    # exact: rho * h^3 (the FP32 path's global mass rescale is off here)
+    # rho * h^3 (the FP32 path's global mass rescale is off here; its warp kernels form the
+    # deposit in float32, so "exactly" means to float32 rounding there)
     m = gpu_tets(tet, [1.0], g, prec, sched, mass_fixup=False)
-    assert m[2, 2, 2] == pytest.approx(ref[2, 2, 2], rel=1e-12)
+    exact_rel = 1e-12 if (prec == pse.PSE_FP64_PLAIN or sched == pse.PSE_THREAD_PER_TET) else 1.2e-7
+    assert m[2, 2, 2] == pytest.approx(ref[2, 2, 2], rel=exact_rel)
     m = gpu_tets(tet, [1.0], g, prec, sched)
     e = cell_errors(m, ref, floor_mass=density_floor(tet, [1.0], g))
     assert e["max_rel"] <= tol_for(prec), e
