@@ -297,6 +297,7 @@ struct WarpSmem {
     int guard[32];        // 1: clip this tetrahedron in float64
     float vlo[12][32];    // guarded tetrahedra: rounding residuals of v (exact = v + vlo)
     unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
+    unsigned long long gq[64]; // queued partial pairs of guarded tetrahedra (float64 clips)
 };
 
 constexpr int kQBits = 19;  // per-axis cell offset bits in a queue entry
@@ -394,37 +395,60 @@ __device__ __forceinline__ bool deposit_pair(const DepositParams &P, const WarpS
     }
 }
 
+// Decode queue entry `ent` of record t: the cell (base-cell frame).
+__device__ __forceinline__ void q_cell(const WarpSmem *S, unsigned long long ent, int &t, int &cx, int &cy, int &cz)
+{
+    t = (int)(ent & 31u);
+    cx = S->lo[0][t] + (int)((ent >> 5) & kQMask);
+    cy = S->lo[1][t] + (int)((ent >> (5 + kQBits)) & kQMask);
+    cz = S->lo[2][t] + (int)((ent >> (5 + 2 * kQBits)) & kQMask);
+}
+
+template <bool STATS, bool OCT>
+__device__ __forceinline__ void deposit_clip(const DepositParams &P, const WarpSmem *S, int t, int cx, int cy, int cz,
+                                             double vol, Counters &cnt)
+{
+    if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
+    if (vol > 0.0) {
+        const double m = (double)(S->rho[t] * (float)vol);
+        cnt.dep += m;
+        if (!deposit_pair<OCT>(P, S, t, cx, cy, cz, m) && STATS) cnt.dropped += m;
+    }
+}
+
+// FP32 clips of the first `count` entries of S->q (tetrahedra below the guard).
 template <bool STATS, bool OCT>
 __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
 {
     if (lane < count) {
-        const unsigned long long ent = S->q[lane];
-        const int t = (int)(ent & 31u);
-        const int cx = S->lo[0][t] + (int)((ent >> 5) & kQMask);
-        const int cy = S->lo[1][t] + (int)((ent >> (5 + kQBits)) & kQMask);
-        const int cz = S->lo[2][t] + (int)((ent >> (5 + 2 * kQBits)) & kQMask);
-        double vol;
-        if (!S->guard[t]) {
-            const float fx = (float)cx, fy = (float)cy, fz = (float)cz;
-            P3<float> p[4];
+        int t, cx, cy, cz;
+        q_cell(S, S->q[lane], t, cx, cy, cz);
+        const float fx = (float)cx, fy = (float)cy, fz = (float)cz;
+        P3<float> p[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                p[q] = mk<float>(S->v[3 * q][t] - fx, S->v[3 * q + 1][t] - fy, S->v[3 * q + 2][t] - fz);
-            P3<float> n[4];
+        for (int q = 0; q < 4; ++q)
+            p[q] = mk<float>(S->v[3 * q][t] - fx, S->v[3 * q + 1][t] - fy, S->v[3 * q + 2][t] - fz);
+        P3<float> n[4];
 #pragma unroll
-            for (int f = 0; f < 4; ++f) n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
-            float err;
-            vol = (double)overlap_volume_ax<float>(p, n, S->axis[t], S->lx[t], S->ly[t], err);
-        } else {
-            vol = redo_fp64(S, t, cx, cy, cz);
-            if (STATS) cnt.u[ST_FP64_REDOS]++;
-        }
-        if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
-        if (vol > 0.0) {
-            const double m = (double)(S->rho[t] * (float)vol);
-            cnt.dep += m;
-            if (!deposit_pair<OCT>(P, S, t, cx, cy, cz, m) && STATS) cnt.dropped += m;
-        }
+        for (int f = 0; f < 4; ++f) n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
+        float err;
+        const double vol = (double)overlap_volume_ax<float>(p, n, S->axis[t], S->lx[t], S->ly[t], err);
+        deposit_clip<STATS, OCT>(P, S, t, cx, cy, cz, vol, cnt);
+    }
+    __syncwarp();
+}
+
+// Float64 clips (exact vertices) of the first `count` entries of S->gq.  Guarded pairs
+// are queued apart so that these rounds run with full warps.
+template <bool STATS, bool OCT>
+__device__ __forceinline__ void redo_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
+{
+    if (lane < count) {
+        int t, cx, cy, cz;
+        q_cell(S, S->gq[lane], t, cx, cy, cz);
+        const double vol = redo_fp64(S, t, cx, cy, cz);
+        if (STATS) cnt.u[ST_FP64_REDOS]++;
+        deposit_clip<STATS, OCT>(P, S, t, cx, cy, cz, vol, cnt);
     }
     __syncwarp();
 }
@@ -446,11 +470,11 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
     S->start[lane] = incl - npairs;
     __syncwarp();
     // one clip_round call site, so that the clip is inlined once (instruction-cache footprint)
-    int qn = 0;
+    int qn = 0, gn = 0;
     for (int b0 = 0;; b0 += 32) {
         if (b0 < total) {
             const int idx = b0 + lane;
-            bool partial = false;
+            bool partial = false, gpartial = false;
             unsigned long long ent = 0;
             if (idx < total) {
                 int t = 0;
@@ -479,13 +503,17 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                         cnt.dropped += m;
                     if (STATS) cnt.u[ST_INSIDE_CELLS]++;
                 } else if (cls == CELL_PARTIAL) {
-                    partial = true;
                     ent = q_pack(t, ix, iy, iz);
+                    if (S->guard[t]) gpartial = true;
+                    else partial = true;
                 }
             }
             const unsigned bal = __ballot_sync(kFull, partial);
             if (partial) S->q[qn + __popc(bal & lt_mask)] = ent;
             qn += __popc(bal);
+            const unsigned gbal = __ballot_sync(kFull, gpartial);
+            if (gpartial) S->gq[gn + __popc(gbal & lt_mask)] = ent;
+            gn += __popc(gbal);
             __syncwarp();
         }
         const bool last = b0 + 32 >= total;
@@ -496,7 +524,14 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
             qn -= take;
             __syncwarp();
         }
-        if (last && qn == 0) break;
+        if (gn >= 32 || (last && gn > 0)) {
+            const int take = gn >= 32 ? 32 : gn;
+            redo_round<STATS, OCT>(P, S, take, lane, cnt);
+            if (lane < gn - take) S->gq[lane] = S->gq[take + lane];
+            gn -= take;
+            __syncwarp();
+        }
+        if (last && qn == 0 && gn == 0) break;
     }
 }
 
