@@ -376,8 +376,32 @@ def test_build_tets_matches_tessellation():
 
 
 # ------------------------------------------------------------ full size ---
-def candidate_cubes(pos, n, cells, g):
-    """Cubes whose (unwrapped) corner bounding box touches any of the given cells."""
+def candidate_cubes(pos, n, cells, g, slab=None):
+    """Cubes whose (unwrapped) corner bounding box touches any of the given cells
+    (z-slabs of `slab` cube layers at a time for large lattices)."""
+    if slab is not None and slab < n:
+        p = pos.reshape(n, n, n, 3)
+        out = []
+        for k0 in range(0, n, slab):
+            k1 = min(n, k0 + slab)
+            rows = np.concatenate([p[k0:k1], p[k1 % n:k1 % n + 1]], 0).astype(np.float64)  # + halo row
+            corners = []
+            for dz in (0, 1):
+                for dy in (0, 1):
+                    for dx in (0, 1):
+                        c = np.roll(rows[dz:dz + (k1 - k0)], shift=(-dy, -dx), axis=(1, 2))
+                        d = c - rows[:k1 - k0]
+                        d -= np.floor(d + 0.5)
+                        corners.append(rows[:k1 - k0] + d)
+            cs = np.stack(corners, 0)
+            lo = np.floor(cs.min(0) * g).astype(np.int64)
+            ext = np.floor(cs.max(0) * g).astype(np.int64) - lo
+            sel = np.zeros(lo.shape[:3], bool)
+            for c in cells:
+                sel |= np.all(np.mod(np.asarray(c) - lo, g) <= ext, axis=-1)
+            kk, jj, ii = np.nonzero(sel)
+            out.append(ii + n * (jj + n * (kk + k0)))
+        return np.sort(np.concatenate(out))
     p = pos.reshape(n, n, n, 3).astype(np.float64)
     corners = []
     for dz in (0, 1):
@@ -403,9 +427,14 @@ def test_config2_full_size_sampled_cells():
     64 random cells checked against the oracle run on every cube that can reach them."""
     cfg = CONFIGS[2]
     pos = config_positions(cfg)
-    m, st = gpu_lattice(pos, cfg.n, cfg.grid_n, pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE, stats=True)
+    # the launch configurations the bench's autotuner chooses among (128-thread blocks per SM)
+    runs = [gpu_lattice(pos, cfg.n, cfg.grid_n, pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE, stats=True,
+                        tuning={"blocks_per_sm": b}) for b in (2, 3, 4)]
+    m, st = runs[1]
     assert st["tets"] == cfg.n_tets
     assert abs(m.sum() - 1.0) <= MASS32
+    for other, _ in (runs[0], runs[2]):
+        assert cell_errors(other, m)["max_rel"] <= 2e-6
     rng = np.random.default_rng(2024)
     g = cfg.grid_n
     cells = [tuple(int(x) for x in rng.integers(0, g, 3)) for _ in range(64)]
@@ -415,6 +444,29 @@ def test_config2_full_size_sampled_cells():
     exp = np.array([ref[c[2], c[1], c[0]] for c in cells])
     den = np.maximum(exp, 1e-3 / g ** 3)
     assert np.max(np.abs(got - exp) / den) <= TOL32
+
+
+def test_config4_full_size_sampled_cells():
+    """512^3 particles (805M tetrahedra, k^-1.5, rms 4 spacings: a fifth of the clips go to the
+    FP64 guard) onto 512^3 in the bench's launch configuration: 8 random cells against the
+    oracle run on every cube that can reach them; mass and counters of the whole deposit."""
+    from pse_inputs import zeldovich_positions_device
+    cfg = CONFIGS[4]
+    pos = zeldovich_positions_device(cfg.n, cfg.spectral_index, cfg.rms_disp, cfg.seed, device="cuda")
+    g = cfg.grid_n
+    m, st = pse.deposit_uniform(pos, cfg.n, g, tuning={"blocks_per_sm": 3}, stats=True)
+    assert st["tets"] == cfg.n_tets
+    m = m.cpu().numpy()
+    assert abs(m.sum() - 1.0) <= MASS32
+    posh = pos.cpu().numpy()
+    del pos
+    rng = np.random.default_rng(4096)
+    cells = [tuple(int(x) for x in rng.integers(0, g, 3)) for _ in range(8)]
+    ids = candidate_cubes(posh, cfg.n, cells, g, slab=64)
+    ref, _ = oracle.deposit_lattice(posh, cfg.n, g, cube_ids=ids, nthreads=4)
+    got = np.array([m[c[2], c[1], c[0]] for c in cells])
+    exp = np.array([ref[c[2], c[1], c[0]] for c in cells])
+    assert np.max(np.abs(got - exp) / np.maximum(exp, 1e-3 / g ** 3)) <= TOL32
 
 
 def test_config2_fp32_vs_fp64_gpu_all_cells():
