@@ -370,7 +370,8 @@ def run_workload(args, cfg):
     max_mhz = csum.get("sm_max_mhz") or 2070.0
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count or SM_COUNT_GB300
-    peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    peaks = pse.measure_peaks(stream)
+    peak = peaks["fp32_tflops"]
     alg = FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] + FLOP_PER_CLIP * st["partial_clips"]
     achieved = alg / (ms * 1e-3) / 1e12
     result = {
@@ -384,7 +385,8 @@ def run_workload(args, cfg):
         "fp64_gpu_baseline": base,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "note": "step time (all kernels of the call)",
-                     "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"},
+                     "peak_source": "measured on this GPU in this run (FP32 FMA microbenchmark); nominal "
+                                    f"{sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 0,
                 "note": "streamed from pinned host memory inside the step" if h2d else
                         "inputs resident (no host copies in this workload's step)"},
@@ -448,6 +450,7 @@ def main():
                                    **kw)
 
     tuned, tune_ms = autotune.tune(call, signature=f"uniform:{cfg.name}", candidates=autotune.UNIFORM_CANDIDATES)
+    peaks = pse.measure_peaks(stream)  # the FP32 and FP64-reduction peaks of this GPU
 
     def step(accumulate=False):
         call(tuned, accumulate=accumulate)
@@ -529,8 +532,10 @@ def main():
         sms = props.multi_processor_count or SM_COUNT_GB300
         csum = clk.summary()
         max_mhz = csum.get("sm_max_mhz") or 2070.0
-        peak = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+        nominal = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+        peak = peaks["fp32_tflops"]
         achieved = alg_flop / (kern_ms * 1e-3) / 1e12
+        deposits = st["partial_clips"] + st["inside_cells"]  # FP64 reductions issued (upper bound)
         cpu = None
         oracle_err = None
         if not args.no_cpu:
@@ -561,7 +566,13 @@ def main():
                          "frac": achieved / peak,
                          "traffic": DRAM_BYTES_PER_LAUNCH if tuned == {"blocks_per_sm": 3, "schedule": "warp"}
                          else None, "traffic_unit": "bytes per launch (ncu dram read + write)",
-                         "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz"},
+                         "peak_source": "measured on this GPU in this run (FP32 FMA microbenchmark, "
+                                        f"{peaks['how'].split(';')[0]}); nominal {sms} SMs x {FP32_LANES_PER_SM}"
+                                        f" lanes x 2 x {max_mhz:.0f} MHz = {nominal:.1f} TFLOP/s"},
+            "atomics": {"achieved_per_s": deposits / (kern_ms * 1e-3), "peak_per_s": peaks["red_f64_per_s"],
+                        "frac": deposits / (kern_ms * 1e-3) / peaks["red_f64_per_s"],
+                        "note": "FP64 global reductions of the deposit kernel against a scattered-reduction "
+                                "microbenchmark measured in this run"},
             "issue": {"thread_inst_per_clip": THREAD_INST_PER_CLIP,
                       "achieved_tinst_per_s": THREAD_INST_PER_CLIP * st["partial_clips"] / (kern_ms * 1e-3),
                       "peak_tinst_per_s": sms * 4 * 32 * max_mhz * 1e6,

@@ -338,6 +338,20 @@ PSE_API int pse_costmodel_train_step(void *d_model, const float *d_feat, const f
                                      void *stream);
 
 /*
+ * Measurement helpers (no counterpart in the paper): the peaks the deposit's roofline is
+ * taken against, measured on the running GPU.  Both enqueue one kernel on `stream`;
+ * time it with events on that stream.
+ *   pse_microbench_fma: `blocks` blocks of 256 threads, each thread running 8 independent
+ *     FP32 FMA chains of `iters` steps: 2 * 8 * iters * 256 * blocks FLOP.  d_out: device
+ *     float32 [blocks * 256] (written only to keep the chains alive).
+ *   pse_microbench_red: `blocks` blocks of 256 threads, each adding 1.0 to `per_thread`
+ *     pseudo-random cells of d_grid (device float64 [n_cells]) with FP64 global reductions.
+ * PSE_ERR_INVALID_ARG for NULL pointers or sizes < 1.
+ */
+PSE_API int pse_microbench_fma(float *d_out, int64_t blocks, int64_t iters, void *stream);
+PSE_API int pse_microbench_red(double *d_grid, int64_t n_cells, int64_t blocks, int64_t per_thread, void *stream);
+
+/*
  * Bytes of device workspace an operation needs.  op = PSE_OP_*; lat may be NULL;
  * op_params: for PSE_OP_BUILD_OCTREE a host int32 max_level (required); for the deposit
  * ops a nullable host pse_deposit_opts (the binned schedule needs room for its queue).

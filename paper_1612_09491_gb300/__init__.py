@@ -330,3 +330,37 @@ def build_octree_streamed(h_pos, n, bc: int, max_level: int, slab_cubes: int, th
                                                      bc, max_level, float(threshold_cells), ctypes.byref(st),
                                                      _stream_ptr(stream)))
     return OctreeHandle(st)
+
+
+def measure_peaks(stream=None, fma_blocks: int = 152 * 8, fma_iters: int = 1 << 16, red_cells: int = 1 << 24,
+                  red_blocks: int = 152 * 8, red_per_thread: int = 4096) -> dict:
+    """FP32 FMA rate and FP64 global-reduction rate of the current GPU (pse_microbench_*),
+    best of 3 timed launches after one warm-up, CUDA events on the stream."""
+    torch = _torch()
+    L = _lib.load()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    out = torch.empty(fma_blocks * 256, dtype=torch.float32, device="cuda")
+    grid = torch.zeros(red_cells, dtype=torch.float64, device="cuda")
+
+    def best(fn):
+        fn()
+        ms = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return min(ms)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    t_fma = best(lambda: _lib.check(L.pse_microbench_fma(ctypes.c_void_p(out.data_ptr()), fma_blocks, fma_iters, sp)))
+    t_red = best(lambda: _lib.check(L.pse_microbench_red(ctypes.c_void_p(grid.data_ptr()), red_cells, red_blocks,
+                                                         red_per_thread, sp)))
+    flop = 2.0 * 8 * fma_iters * 256 * fma_blocks
+    reds = float(red_per_thread) * 256 * red_blocks
+    return {"fp32_tflops": flop / (t_fma * 1e-3) / 1e12, "red_f64_per_s": reds / (t_red * 1e-3),
+            "fma_ms": t_fma, "red_ms": t_red,
+            "how": f"{fma_blocks} x 256 threads x 8 FMA chains x {fma_iters} steps; {red_blocks} x 256 threads x "
+                   f"{red_per_thread} FP64 reductions over {red_cells} cells (8-byte, pseudo-random)"}

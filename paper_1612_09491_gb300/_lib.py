@@ -50,6 +50,8 @@ EXPORTED = (
     "pse_deposit_uniform_streamed",
     "pse_deposit_octree_streamed",
     "pse_build_octree_streamed",
+    "pse_microbench_fma",
+    "pse_microbench_red",
     "pse_costmodel_bytes",
     "pse_costmodel_set",
     "pse_costmodel_get",
@@ -155,6 +157,10 @@ def load(build_if_missing: bool = False):
         L.pse_build_octree_streamed.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int64, ctypes.c_int32,
                                                 ctypes.c_int32, ctypes.c_double, OP, vp]
         L.pse_build_octree_streamed.restype = ctypes.c_int
+        L.pse_microbench_fma.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, vp]
+        L.pse_microbench_fma.restype = ctypes.c_int
+        L.pse_microbench_red.argtypes = [vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, vp]
+        L.pse_microbench_red.restype = ctypes.c_int
         L.pse_costmodel_bytes.argtypes = []
         L.pse_costmodel_bytes.restype = ctypes.c_size_t
         L.pse_costmodel_set.argtypes = [vp, vp, vp]
