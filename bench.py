@@ -525,6 +525,12 @@ def main():
             err = cell_errors(fast_grid, out.cpu().numpy())
             base = {"tets_per_s": n_tets / (bms * 1e-3), "ms_per_step": bms, "speedup": (n_tets / (ms * 1e-3)) /
                     (n_tets / (bms * 1e-3)), "error_of_timed_arm": err}
+            # the paper's GPU design (one warp per tetrahedron, Sec. 6.2) with the same clip
+            pms = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=prec,
+                                                     schedule=pse.PSE_WARP_PER_TET), 3, 1, flush, stream)
+            pms = sum(pms) / len(pms)
+            base["paper_design_warp_per_tet"] = {"tets_per_s": n_tets / (pms * 1e-3), "ms_per_step": pms,
+                                                 "speedup_of_timed_arm": pms / ms}
         # roofline of the dominant kernel (FP32 ALU bound)
         alg_flop = (FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] +
                     FLOP_PER_CLIP * st["partial_clips"])

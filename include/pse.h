@@ -78,6 +78,10 @@ extern "C" {
                                    bounding box exceeds pse_tuning.split_cells; one persistent kernel
                                    takes work items (pieces of the queued tetrahedra first, then rows of
                                    cubes) from one atomic counter.  FP32 path, uniform grids. */
+#define PSE_WARP_PER_TET 3      /* the paper's GPU kernel design (Sec. 6.2) on this GPU, kept as a baseline:
+                                   one warp per tetrahedron, lanes striding over its bounding-box cells,
+                                   partial cells buffered in shared memory and clipped 32 at a time.  FP32
+                                   path, uniform grids (octree deposits use the warp-cooperative kernel). */
 
 /* operation ids for pse_workspace_size */
 #define PSE_OP_DEPOSIT_UNIFORM 1
@@ -261,6 +265,20 @@ PSE_API void pse_free_octree(pse_octree *oct);
 PSE_API int pse_build_octree_leaves_noalloc(const float *d_pos, const pse_lattice *lat, int32_t bc,
                                             int32_t max_level, double edge_threshold_cells, int32_t *d_leaves,
                                             int64_t cap, int64_t *d_n_leaves, void *stream);
+
+/*
+ * Coarse node masses for multi-resolution use (the paper keeps the masses of the inner
+ * nodes of its adaptive grid for rendering at several resolutions, Sec. 8): every node of
+ * levels 0 .. max_level-1 gets its own bc^3 block of cell masses.
+ *   d_leaf_mass  device float64 [n_leaves * bc^3], as written by pse_deposit_octree.
+ *   d_pyramid    device float64 [P * bc^3], P = sum_{l < max_level} 8^l; node (l, x, y, z)
+ *                is row (8^0 + ... + 8^(l-1)) + x + 2^l (y + 2^l z), cells x fastest.
+ *                A leaf's row is its block; an inner node's cell holds the sum of the 8
+ *                cells of the level below that it covers; a node below a leaf is 0.
+ * For every node of the tree the row equals the deposit on the uniform grid of that
+ * level restricted to the node.  Asynchronous.
+ */
+PSE_API int pse_octree_restrict(const pse_octree *oct, const double *d_leaf_mass, double *d_pyramid, void *stream);
 
 /*
  * Slab streaming (periodic lattices whose positions live in host memory): the lattice

@@ -15,6 +15,7 @@ from ._lib import (  # noqa: F401
     PSE_FP32_FP64ACC,
     PSE_FP64_PLAIN,
     PSE_THREAD_PER_TET,
+    PSE_WARP_PER_TET,
     PSE_WARP_COOPERATIVE,
     PseError,
 )
@@ -364,3 +365,17 @@ def measure_peaks(stream=None, fma_blocks: int = 152 * 8, fma_iters: int = 1 << 
             "fma_ms": t_fma, "red_ms": t_red,
             "how": f"{fma_blocks} x 256 threads x 8 FMA chains x {fma_iters} steps; {red_blocks} x 256 threads x "
                    f"{red_per_thread} FP64 reductions over {red_cells} cells (8-byte, pseudo-random)"}
+
+
+def octree_restrict(octree: OctreeHandle, leaf_mass, stream=None):
+    """pse_octree_restrict: float64 [P, bc, bc, bc] masses of every node of levels 0..max_level-1
+    (row of node (l, x, y, z): sum_{k<l} 8^k + x + 2^l (y + 2^l z))."""
+    torch = _torch()
+    bc, ml = octree.bc, octree.max_level
+    rows = sum(8 ** k for k in range(ml))
+    out = torch.empty((max(rows, 0), bc, bc, bc), dtype=torch.float64, device=leaf_mass.device)
+    if rows == 0:
+        return out
+    _lib.check(_lib.load().pse_octree_restrict(ctypes.byref(octree.st), _dev_ptr(leaf_mass, torch.float64, "leaf_mass"),
+                                               _dev_ptr(out, torch.float64, "out"), _stream_ptr(stream)))
+    return out

@@ -27,6 +27,7 @@ PSE_FP32_FP64ACC = 1
 PSE_THREAD_PER_TET = 0
 PSE_WARP_COOPERATIVE = 1
 PSE_BINNED_PERSISTENT = 2
+PSE_WARP_PER_TET = 3
 
 PSE_OP_DEPOSIT_UNIFORM = 1
 PSE_OP_DEPOSIT_OCTREE = 2
@@ -47,6 +48,7 @@ EXPORTED = (
     "pse_deposit_octree",
     "pse_free_octree",
     "pse_build_octree_leaves_noalloc",
+    "pse_octree_restrict",
     "pse_deposit_uniform_streamed",
     "pse_deposit_octree_streamed",
     "pse_build_octree_streamed",
@@ -146,6 +148,8 @@ def load(build_if_missing: bool = False):
         L.pse_build_octree_leaves_noalloc.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int32, ctypes.c_int32,
                                                       ctypes.c_double, vp, ctypes.c_int64, vp, vp]
         L.pse_build_octree_leaves_noalloc.restype = ctypes.c_int
+        L.pse_octree_restrict.argtypes = [OP, vp, vp, vp]
+        L.pse_octree_restrict.restype = ctypes.c_int
         L.pse_deposit_uniform_streamed.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int64,
                                                    ctypes.POINTER(ctypes.c_int64), vp, ctypes.POINTER(DepositOpts),
                                                    ctypes.POINTER(DepositStats), vp, ctypes.c_size_t, vp]

@@ -138,7 +138,8 @@ int check_opts(const pse_deposit_opts &o)
 {
     if (o.precision != PSE_FP64_PLAIN && o.precision != PSE_FP32_FP64ACC)
         return fail(PSE_ERR_INVALID_ARG, "unknown precision %d", o.precision);
-    if (o.schedule != PSE_THREAD_PER_TET && o.schedule != PSE_WARP_COOPERATIVE && o.schedule != PSE_BINNED_PERSISTENT)
+    if (o.schedule != PSE_THREAD_PER_TET && o.schedule != PSE_WARP_COOPERATIVE && o.schedule != PSE_BINNED_PERSISTENT &&
+        o.schedule != PSE_WARP_PER_TET)
         return fail(PSE_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
     if (o.schedule != PSE_THREAD_PER_TET && o.precision == PSE_FP64_PLAIN)
         return fail(PSE_ERR_UNSUPPORTED, "the warp-cooperative and binned schedules run the FP32 clip (precision 1)");
@@ -290,6 +291,7 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
             if (e != cudaSuccess) return cuda_fail(e, "octree deposit launch");
         } else {
             if (o.schedule == PSE_THREAD_PER_TET) e = pse::launch_thread_per_tet(q, o.precision == PSE_FP64_PLAIN, stats, s);
+            else if (o.schedule == PSE_WARP_PER_TET) e = pse::launch_warp_per_tet(q, stats, s);
             else if (binned) e = pse::launch_binned(q, stats, bps, s);
             else e = pse::launch_warp_coop(q, stats, bps, s);
             if (e != cudaSuccess) return cuda_fail(e, "deposit launch");
@@ -760,6 +762,19 @@ int pse_deposit_tets(const float *d_verts, const double *d_tet_mass, int64_t n_t
     fill_grid(p, grid_n, box);
     p.out = d_cell_mass;
     return run_deposit(p, o, cells, h_stats, d_ws, ws_bytes, static_cast<cudaStream_t>(stream));
+}
+
+// ---------------------------------------------------------------------------
+// restriction up the octree
+// ---------------------------------------------------------------------------
+int pse_octree_restrict(const pse_octree *oct, const double *d_leaf_mass, double *d_pyramid, void *stream)
+{
+    g_last_error.clear();
+    if (!oct || !d_leaf_mass || !d_pyramid) return fail(PSE_ERR_INVALID_ARG, "oct, d_leaf_mass and d_pyramid must be non-NULL");
+    if (!oct->d_leaves || !oct->d_fine_map || oct->n_leaves < 1) return fail(PSE_ERR_INVALID_ARG, "oct is empty");
+    cudaError_t e = pse::launch_octree_restrict(oct->d_fine_map, oct->d_leaves, oct->max_level, oct->bc, d_leaf_mass,
+                                                d_pyramid, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? PSE_OK : cuda_fail(e, "restriction launch");
 }
 
 // ---------------------------------------------------------------------------

@@ -301,6 +301,80 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
 }
 
 // ---------------------------------------------------------------------------
+// the paper's design (Sec. 6.2), kept as a baseline: one warp per tetrahedron; its
+// bounding-box cells are classified 32 at a time and the partial ones buffered and
+// clipped 32 at a time (the same pair machinery and clip, with one record per warp)
+// ---------------------------------------------------------------------------
+template <bool STATS>
+__global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    Counters cnt;
+    if (STATS) cnt.zero();
+    cnt.zero_mass();
+    const int64_t n_tets = (P.src == SRC_TETS) ? P.n_units : 6 * P.n_units;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(&P.ws->work_counter, 1ull);
+        t = __shfl_sync(kFull, t, 0);
+        if ((int64_t)t >= n_tets) break;
+        int npairs = 0;
+        if (lane == 0) {
+            P3<float> v[4], res[4];
+            int base[3];
+            double m_t;
+            bool ok = true;
+            if (P.src == SRC_TETS) {
+                explicit_tet<float>(P, (int64_t)t, v, base, res);
+                m_t = P.tet_mass[t];
+            } else {
+                int64_t ci, cj, ck;
+                ok = cube_of_unit(P, (int64_t)t / 6, ci, cj, ck);
+                if (!ok) set_error(P.ws, 3, (int)(((int64_t)t / 6) & 0x7fffffff));
+                if (ok) lattice_tet<float>(P, ci, cj, ck, (int)(t % 6), v, base, res);
+                m_t = P.m_tet;
+            }
+            if (ok) {
+                TetSetup<float> ts;
+                if (tet_setup<float>(v, ts)) swap12(res);
+                if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+                const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
+                if (!tet_ok(base, ts)) {
+                    set_error(P.ws, 4, (int)(t & 0x7fffffff));
+                } else if (ts.vol6 == 0.0 || ncell == 1) {
+                    int c[3];
+                    if (ts.vol6 == 0.0) centroid_cell(ts.v, c);
+                    else { c[0] = ts.lo[0]; c[1] = ts.lo[1]; c[2] = ts.lo[2]; }
+                    if (!deposit_cell(P, (int64_t)base[0] + c[0], (int64_t)base[1] + c[1], (int64_t)base[2] + c[2], m_t) &&
+                        STATS)
+                        cnt.dropped += m_t;
+                    cnt.tgt += m_t;
+                    cnt.dep += m_t;
+                    if (STATS) {
+                        cnt.u[ts.vol6 == 0.0 ? ST_DEGENERATE : ST_SINGLE_CELL]++;
+                        if (ts.vol6 != 0.0) { cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
+                    }
+                } else if (ncell > (int64_t)(1 << 25)) {
+                    set_error(P.ws, 2, (int)(t & 0x7fffffff));
+                } else {
+                    npairs = (int)ncell;
+                    cnt.tgt += m_t;
+                    if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
+                    store_record(S, 0, ts, res, base, m_t, P.kappa_max, 0);
+                }
+            }
+        }
+        __syncwarp();
+        coop_pairs<STATS, false>(P, S, lane, npairs, cnt);
+        __syncwarp();
+    }
+    if (STATS) cnt.flush(P.ws);
+    if (P.fixup) cnt.flush_mass(P.ws);
+}
+
+// ---------------------------------------------------------------------------
 // binned schedule: the bin pass queues every tetrahedron whose bounding box has more
 // than split_cells cells (warp-aggregated appends); the scan turns their cell counts
 // into work items of chunk_cells cells.
@@ -518,6 +592,18 @@ cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, i
 cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st)
 {
     return launch_coop<false>(p, stats, blocks_per_sm, p.n_items, st);
+}
+
+cudaError_t launch_warp_per_tet(const DepositParams &p, bool stats, cudaStream_t st)
+{
+    const int threads = kCoopThreads;
+    const size_t smem = sizeof(WarpSmem) * (threads / 32);
+    const void *k = stats ? (const void *)k_warp_per_tet<true> : (const void *)k_warp_per_tet<false>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int blocks = persistent_blocks(k, threads, smem);
+    void *args[] = {const_cast<DepositParams *>(&p)};
+    return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
 }
 
 cudaError_t launch_binned(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st)

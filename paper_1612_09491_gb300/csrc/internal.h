@@ -98,6 +98,7 @@ void set_last_error(const char *msg);
 cudaError_t launch_thread_per_tet(const DepositParams &p, bool fp64, bool stats, cudaStream_t st);
 cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_binned(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st);
+cudaError_t launch_warp_per_tet(const DepositParams &p, bool stats, cudaStream_t st);
 
 // cost model (costmodel.cu)
 struct CostModelDev;
@@ -114,6 +115,8 @@ cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStrea
 cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread_per_tet, bool stats,
                                   int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_scale(double *out, int64_t n, const Workspace *ws, cudaStream_t st);
+cudaError_t launch_octree_restrict(const int32_t *fine_map, const int32_t *leaves, int max_level, int bc,
+                                   const double *leaf_mass, double *pyramid, cudaStream_t st);
 cudaError_t launch_build_tets(const float *pos, const int64_t n[3], const int64_t nc[3], int periodic,
                               double box, int32_t *vidx, float *vol, int64_t n_tets, cudaStream_t st);
 

@@ -532,6 +532,83 @@ __global__ void __launch_bounds__(256) k_tet_size_hist(const DepositParams P, un
 
 }  // namespace
 
+namespace {
+// ---------------------------------------------------------------------------
+// Restriction up the tree: the masses of every node of levels 0 .. max_level-1 on its
+// own bc^3 block (leaves: their block; internal nodes: each cell the sum of the 8 cells
+// of the level below that it covers; nodes below a leaf: 0).  One launch per level,
+// finest first, so that an internal node's children are complete when it is summed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t level_offset(int l)
+{
+    int64_t o = 0;
+    for (int k = 0; k < l; ++k) o += (int64_t)1 << (3 * k);
+    return o;
+}
+
+// leaf record of the finest node below node (l, x, y, z), and its level
+__device__ __forceinline__ int leaf_below(const int32_t *fine_map, const int32_t *leaves, int max_level, int l,
+                                          int64_t x, int64_t y, int64_t z, int &leaf_level)
+{
+    const int64_t F = (int64_t)1 << max_level, s = (int64_t)1 << (max_level - l);
+    const int leaf = fine_map[x * s + F * (y * s + F * (z * s))];
+    leaf_level = leaves[4 * leaf];
+    return leaf;
+}
+
+__global__ void __launch_bounds__(256) k_restrict_level(const int32_t *__restrict__ fine_map,
+                                                        const int32_t *__restrict__ leaves, int max_level, int bc,
+                                                        int l, const double *__restrict__ leaf_mass,
+                                                        double *__restrict__ pyramid)
+{
+    const int64_t nn = (int64_t)1 << l, bc3 = (int64_t)bc * bc * bc;
+    const int64_t total = nn * nn * nn * bc3;
+    const int64_t row0 = level_offset(l), row1 = level_offset(l + 1);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t node = idx / bc3, cell = idx % bc3;
+        const int64_t nx = node % nn, ny = (node / nn) % nn, nz = node / (nn * nn);
+        const int ci = (int)(cell % bc), cj = (int)((cell / bc) % bc), ck = (int)(cell / ((int64_t)bc * bc));
+        int ll;
+        const int leaf = leaf_below(fine_map, leaves, max_level, l, nx, ny, nz, ll);
+        double v = 0.0;
+        if (ll == l) {
+            v = leaf_mass[(int64_t)leaf * bc3 + cell];
+        } else if (ll > l) {
+            for (int d = 0; d < 8; ++d) {
+                const int fx = 2 * ci + (d & 1), fy = 2 * cj + ((d >> 1) & 1), fz = 2 * ck + (d >> 2);
+                const int64_t cx = 2 * nx + fx / bc, cy = 2 * ny + fy / bc, cz = 2 * nz + fz / bc;
+                const int64_t lc = (fx % bc) + (int64_t)bc * ((fy % bc) + (int64_t)bc * (fz % bc));
+                int cl;
+                const int cleaf = leaf_below(fine_map, leaves, max_level, l + 1, cx, cy, cz, cl);
+                if (cl == l + 1) {
+                    v += leaf_mass[(int64_t)cleaf * bc3 + lc];
+                } else {
+                    const int64_t cn = 2 * nn;
+                    v += pyramid[(row1 + cx + cn * (cy + cn * cz)) * bc3 + lc];
+                }
+            }
+        }
+        pyramid[(row0 + node) * bc3 + cell] = v;
+    }
+}
+}  // namespace
+
+cudaError_t launch_octree_restrict(const int32_t *fine_map, const int32_t *leaves, int max_level, int bc,
+                                   const double *leaf_mass, double *pyramid, cudaStream_t st)
+{
+    for (int l = max_level - 1; l >= 0; --l) {
+        const int64_t total = ((int64_t)1 << (3 * l)) * (int64_t)bc * bc * bc;
+        int64_t blocks = (total + 255) / 256;
+        if (blocks > 152 * 64) blocks = 152 * 64;
+        if (blocks < 1) blocks = 1;
+        k_restrict_level<<<(unsigned)blocks, 256, 0, st>>>(fine_map, leaves, max_level, bc, l, leaf_mass, pyramid);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStream_t st)
 {
     const int threads = 256;

@@ -193,3 +193,34 @@ def test_octree_graph_replay():
             pse.deposit_octree(pos, n, oct_, out=out, workspace=ws, tuning={"use_graph": 1})
             e = cell_errors(out.cpu().numpy(), ref)
             assert e["max_rel"] <= 2e-6 and e["mass"] <= 1e-13, e
+
+
+def test_restriction_equals_coarse_uniform_deposits():
+    """Every node of levels 0..max_level-1 (pse_octree_restrict) holds the deposit on the
+    uniform grid of its level restricted to the node; nodes below a leaf hold 0."""
+    n, bc, ml = 16, 4, 4
+    pos = squeezed_lattice(n)
+    leaves, _ = oracle.build_octree(pos, n, bc, ml)
+    assert len(set(leaves[:, 0].tolist())) > 1
+    oct_ = pse.octree_from_leaves(leaves, bc, ml)
+    m = pse.deposit_octree(torch.from_numpy(pos).cuda(), n, oct_, precision=pse.PSE_FP64_PLAIN,
+                           schedule=pse.PSE_THREAD_PER_TET)
+    pyr = pse.octree_restrict(oct_, m).cpu().numpy()
+    row = 0
+    for l in range(ml):
+        nn = 2 ** l
+        ref, _ = oracle.deposit_lattice(pos, n, bc * nn)
+        floor = 1e-3 * ref.mean()
+        for z in range(nn):
+            for y in range(nn):
+                for x in range(nn):
+                    blk = pyr[row + x + nn * (y + nn * z)]
+                    # where is this node: a leaf, an inner node, or below a coarser leaf?
+                    below = any(L[0] < l and all((c >> (l - L[0])) == L[1 + a] for a, c in enumerate((x, y, z)))
+                                for L in leaves)
+                    if below:
+                        assert not blk.any()
+                        continue
+                    r = ref[z * bc:(z + 1) * bc, y * bc:(y + 1) * bc, x * bc:(x + 1) * bc]
+                    assert np.max(np.abs(blk - r) / np.maximum(r, floor)) <= 1e-9, (l, x, y, z)
+        row += nn ** 3

@@ -33,6 +33,7 @@ PATHS = [
     ("fp32-thread", pse.PSE_FP32_FP64ACC, pse.PSE_THREAD_PER_TET),
     ("fp32-warp", pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE),
     ("fp32-binned", pse.PSE_FP32_FP64ACC, "binned"),
+    ("fp32-warp-per-tet", pse.PSE_FP32_FP64ACC, pse.PSE_WARP_PER_TET),
 ]
 # the binned schedule with tiny thresholds, so that small cases go through the split
 # work items (every tetrahedron with more than 4 bounding-box cells, 8 cells per item)
