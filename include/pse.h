@@ -267,6 +267,19 @@ PSE_API int pse_build_octree_leaves_noalloc(const float *d_pos, const pse_lattic
                                             int64_t cap, int64_t *d_n_leaves, void *stream);
 
 /*
+ * The paper's own refinement criterion (Sec. 4), as an alternative to the size rule of
+ * pse_build_octree_from_tet_sizes: the Lagrangian lattice is cut into subblocks of
+ * subblock^3 cubes (the paper uses 8^3); the axis-aligned bounding box of each subblock's
+ * particles stands for its tetrahedra, assumed spread evenly over the box.  A node is
+ * refined while the estimated number of tetrahedra overlapping it,
+ *     sum over subblocks of 6 * cubes * vol(box ∩ node) / vol(box)   (periodic images),
+ * exceeds count_threshold and its level is below max_level (the minimal node size).
+ * Leaves and output as for pse_build_octree_from_tet_sizes.  Synchronous.
+ */
+PSE_API int pse_build_octree_count(const float *d_pos, const pse_lattice *lat, int32_t bc, int32_t max_level,
+                                   double count_threshold, int32_t subblock, pse_octree *out, void *stream);
+
+/*
  * Coarse node masses for multi-resolution use (the paper keeps the masses of the inner
  * nodes of its adaptive grid for rendering at several resolutions, Sec. 8): every node of
  * levels 0 .. max_level-1 gets its own bc^3 block of cell masses.

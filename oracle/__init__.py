@@ -224,3 +224,60 @@ def deposit_octree(pos, n, leaves, bc: int, max_level: int, box: float = 1.0, pe
     if rc != 0:
         raise RuntimeError(f"oracle_deposit_octree failed: {rc}")
     return out.reshape(nl, bc, bc, bc), dict(zip(STAT_KEYS, st.tolist()))
+
+
+def build_octree_count(pos, n, bc: int, max_level: int, count_threshold: float, subblock: int = 8,
+                       box: float = 1.0):
+    """The refinement rule of Sec. 4 in plain float64 numpy: subblocks of subblock^3 cubes, the
+    bounding box of each subblock's (unwrapped) particles, the estimated tetrahedra per node
+    sum_b 6 cubes_b vol(box_b ∩ node) / vol(box_b) over periodic images; refine while the
+    estimate exceeds count_threshold and level < max_level.  Returns (leaves [L, 4] depth first,
+    {(level, ix, iy, iz): estimate} of every evaluated node)."""
+    p = np.asarray(pos, dtype=np.float64).reshape(n, n, n, 3)  # [k, j, i, axis]
+    nbl = (n + subblock - 1) // subblock
+    boxes = []
+    for bz in range(nbl):
+        for by in range(nbl):
+            for bx in range(nbl):
+                i0, j0, k0 = bx * subblock, by * subblock, bz * subblock
+                i1, j1, k1 = min(n, i0 + subblock), min(n, j0 + subblock), min(n, k0 + subblock)
+                ii = np.arange(i0, i1 + 1) % n
+                jj = np.arange(j0, j1 + 1) % n
+                kk = np.arange(k0, k1 + 1) % n
+                pts = p[np.ix_(kk, jj, ii)].reshape(-1, 3)
+                ref = p[k0, j0, i0]
+                d = pts - ref
+                d -= np.where(d >= 0.5 * box, box, np.where(d < -0.5 * box, -box, 0.0))
+                q = ref + d
+                boxes.append((q.min(0), q.max(0), 6.0 * (i1 - i0) * (j1 - j0) * (k1 - k0)))
+
+    def overlap(lo, hi, x0, x1):
+        return sum(max(min(hi + s * box, x1) - max(lo + s * box, x0), 0.0) for s in (-1, 0, 1))
+
+    est = {}
+
+    def visit(level, ix, iy, iz, leaves):
+        refine = False
+        if level < max_level:
+            size = box / 2 ** level
+            x0 = np.array([ix, iy, iz]) * size
+            total = 0.0
+            for lo, hi, tets in boxes:
+                vol = float(np.prod(hi - lo))
+                if not vol > 0.0:
+                    continue
+                ov = 1.0
+                for a in range(3):
+                    ov *= overlap(lo[a], hi[a], x0[a], x0[a] + size)
+                total += tets * ov / vol
+            est[(level, ix, iy, iz)] = total
+            refine = total > count_threshold
+        if not refine:
+            leaves.append((level, ix, iy, iz))
+            return
+        for c in range(8):
+            visit(level + 1, 2 * ix + (c & 1), 2 * iy + ((c >> 1) & 1), 2 * iz + (c >> 2), leaves)
+
+    leaves = []
+    visit(0, 0, 0, 0, leaves)
+    return np.array(leaves, dtype=np.int32), est

@@ -379,3 +379,15 @@ def octree_restrict(octree: OctreeHandle, leaf_mass, stream=None):
     _lib.check(_lib.load().pse_octree_restrict(ctypes.byref(octree.st), _dev_ptr(leaf_mass, torch.float64, "leaf_mass"),
                                                _dev_ptr(out, torch.float64, "out"), _stream_ptr(stream)))
     return out
+
+
+def build_octree_count(pos, n, bc: int, max_level: int, count_threshold: float, subblock: int = 8, *,
+                       box: float = 1.0, stream=None) -> OctreeHandle:
+    """pse_build_octree_count: the paper's refinement rule (estimated tetrahedra per node)."""
+    torch = _torch()
+    lat = lattice(n, box, True)
+    st = _lib.Octree()
+    _lib.check(_lib.load().pse_build_octree_count(_dev_ptr(pos, torch.float32, "pos"), ctypes.byref(lat), bc,
+                                                  max_level, float(count_threshold), int(subblock),
+                                                  ctypes.byref(st), _stream_ptr(stream)))
+    return OctreeHandle(st)

@@ -48,6 +48,7 @@ EXPORTED = (
     "pse_deposit_octree",
     "pse_free_octree",
     "pse_build_octree_leaves_noalloc",
+    "pse_build_octree_count",
     "pse_octree_restrict",
     "pse_deposit_uniform_streamed",
     "pse_deposit_octree_streamed",
@@ -148,6 +149,9 @@ def load(build_if_missing: bool = False):
         L.pse_build_octree_leaves_noalloc.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int32, ctypes.c_int32,
                                                       ctypes.c_double, vp, ctypes.c_int64, vp, vp]
         L.pse_build_octree_leaves_noalloc.restype = ctypes.c_int
+        L.pse_build_octree_count.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_int32, OP, vp]
+        L.pse_build_octree_count.restype = ctypes.c_int
         L.pse_octree_restrict.argtypes = [OP, vp, vp, vp]
         L.pse_octree_restrict.restype = ctypes.c_int
         L.pse_deposit_uniform_streamed.argtypes = [vp, ctypes.POINTER(Lattice), ctypes.c_int64,

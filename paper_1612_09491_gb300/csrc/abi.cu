@@ -765,6 +765,88 @@ int pse_deposit_tets(const float *d_verts, const double *d_tet_mass, int64_t n_t
 }
 
 // ---------------------------------------------------------------------------
+// the paper's count criterion
+// ---------------------------------------------------------------------------
+namespace {
+void emit_leaves(const std::vector<std::vector<char>> &refine, int level, int64_t ix, int64_t iy, int64_t iz,
+                 std::vector<int32_t> &leaves)
+{
+    const int64_t nn = (int64_t)1 << level;
+    const bool r = level < (int)refine.size() && refine[level][(size_t)(ix + nn * (iy + nn * iz))];
+    if (!r) {
+        leaves.push_back(level);
+        leaves.push_back((int32_t)ix);
+        leaves.push_back((int32_t)iy);
+        leaves.push_back((int32_t)iz);
+        return;
+    }
+    for (int c = 0; c < 8; ++c)
+        emit_leaves(refine, level + 1, 2 * ix + (c & 1), 2 * iy + ((c >> 1) & 1), 2 * iz + (c >> 2), leaves);
+}
+}  // namespace
+
+int pse_build_octree_count(const float *d_pos, const pse_lattice *lat, int32_t bc, int32_t max_level,
+                           double count_threshold, int32_t subblock, pse_octree *out, void *stream)
+{
+    g_last_error.clear();
+    int rc = check_lattice(lat);
+    if (rc != PSE_OK) return rc;
+    if (!d_pos || !out) return fail(PSE_ERR_INVALID_ARG, "d_pos and out must be non-NULL");
+    if (!lat->periodic) return fail(PSE_ERR_UNSUPPORTED, "the octree covers a periodic box");
+    if (bc < 1 || bc > 4096) return fail(PSE_ERR_INVALID_ARG, "bc = %d out of range [1, 4096]", bc);
+    if (max_level < 0 || max_level > kMaxOctreeLevel) return fail(PSE_ERR_INVALID_ARG, "max_level out of range");
+    if (!(count_threshold > 0.0)) return fail(PSE_ERR_INVALID_ARG, "count_threshold must be > 0");
+    if (subblock < 1) return fail(PSE_ERR_INVALID_ARG, "subblock must be >= 1");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t nb = ((lat->n[0] + subblock - 1) / subblock) * ((lat->n[1] + subblock - 1) / subblock) *
+                       ((lat->n[2] + subblock - 1) / subblock);
+    const int64_t max_nodes = max_level > 0 ? ((int64_t)1 << (3 * (max_level - 1))) : 1;
+    double *d_boxes = nullptr, *d_counts = nullptr;
+    int32_t *d_nodes = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&d_boxes), (size_t)nb * 7 * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_counts), (size_t)max_nodes * sizeof(double), st);
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void **>(&d_nodes), (size_t)max_nodes * 4 * sizeof(int32_t), st);
+    if (e == cudaSuccess) e = pse::launch_subblock_boxes(d_pos, lat->n, subblock, lat->box, d_boxes, st);
+    // level by level: the nodes whose parent was refined, their estimated counts, the decisions
+    std::vector<std::vector<char>> refine;
+    std::vector<int32_t> nodes = {0, 0, 0, 0};
+    for (int l = 0; l < max_level && e == cudaSuccess && !nodes.empty(); ++l) {
+        const int64_t nn = (int64_t)1 << l;
+        refine.emplace_back((size_t)(nn * nn * nn), 0);
+        const int64_t cnt = (int64_t)nodes.size() / 4;
+        std::vector<double> counts((size_t)cnt);
+        e = cudaMemcpyAsync(d_nodes, nodes.data(), nodes.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = pse::launch_node_counts(d_boxes, nb, d_nodes, cnt, lat->box, d_counts, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(counts.data(), d_counts, (size_t)cnt * sizeof(double),
+                                                  cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        std::vector<int32_t> next;
+        for (int64_t i = 0; i < cnt; ++i) {
+            if (!(counts[(size_t)i] > count_threshold)) continue;
+            const int32_t x = nodes[4 * i + 1], y = nodes[4 * i + 2], z = nodes[4 * i + 3];
+            refine[(size_t)l][(size_t)(x + nn * (y + nn * z))] = 1;
+            if (l + 1 < max_level)
+                for (int c = 0; c < 8; ++c) {
+                    next.push_back(l + 1);
+                    next.push_back(2 * x + (c & 1));
+                    next.push_back(2 * y + ((c >> 1) & 1));
+                    next.push_back(2 * z + (c >> 2));
+                }
+        }
+        nodes.swap(next);
+    }
+    cudaFreeAsync(d_boxes, st);
+    cudaFreeAsync(d_counts, st);
+    cudaFreeAsync(d_nodes, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "octree counts");
+    std::vector<int32_t> leaves;
+    emit_leaves(refine, 0, 0, 0, 0, leaves);
+    return make_octree(leaves.data(), (int64_t)(leaves.size() / 4), bc, max_level, lat->box, out);
+}
+
+// ---------------------------------------------------------------------------
 // restriction up the octree
 // ---------------------------------------------------------------------------
 int pse_octree_restrict(const pse_octree *oct, const double *d_leaf_mass, double *d_pyramid, void *stream)

@@ -115,6 +115,10 @@ cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStrea
 cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread_per_tet, bool stats,
                                   int blocks_per_sm, cudaStream_t st);
 cudaError_t launch_scale(double *out, int64_t n, const Workspace *ws, cudaStream_t st);
+cudaError_t launch_subblock_boxes(const float *pos, const int64_t n[3], int s, double box, double *boxes,
+                                  cudaStream_t st);
+cudaError_t launch_node_counts(const double *boxes, int64_t nb, const int32_t *nodes, int64_t n_nodes, double box,
+                               double *counts, cudaStream_t st);
 cudaError_t launch_octree_restrict(const int32_t *fine_map, const int32_t *leaves, int max_level, int bc,
                                    const double *leaf_mass, double *pyramid, cudaStream_t st);
 cudaError_t launch_build_tets(const float *pos, const int64_t n[3], const int64_t nc[3], int periodic,

@@ -609,6 +609,109 @@ cudaError_t launch_octree_restrict(const int32_t *fine_map, const int32_t *leave
     return cudaSuccess;
 }
 
+namespace {
+// ---------------------------------------------------------------------------
+// The paper's refinement criterion (Sec. 4): the Lagrangian lattice is cut into
+// subblocks of S^3 cubes; the axis-aligned bounding box of each subblock's particles
+// (unwrapped around its first particle) stands for its 6 S^3 tetrahedra, spread evenly.
+// A node's estimated tetrahedron count is the sum over subblocks of 6 * cubes *
+// vol(box ∩ node) / vol(box), periodic images included.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_subblock_boxes(const float *__restrict__ pos, int64_t n0, int64_t n1,
+                                                        int64_t n2, int s, double box, double *__restrict__ boxes)
+{
+    const int64_t b0 = (n0 + s - 1) / s, b1 = (n1 + s - 1) / s, b2 = (n2 + s - 1) / s;
+    const int64_t nb = b0 * b1 * b2;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bx = b % b0, by = (b / b0) % b1, bz = b / (b0 * b1);
+        const int64_t i0 = bx * s, j0 = by * s, k0 = bz * s;
+        const int64_t i1 = min(n0, i0 + s), j1 = min(n1, j0 + s), k1 = min(n2, k0 + s);  // cubes [i0, i1)
+        const float *r = pos + 3 * (i0 + n0 * (j0 + n1 * k0));
+        const double rx = r[0], ry = r[1], rz = r[2];
+        double lo[3] = {rx, ry, rz}, hi[3] = {rx, ry, rz};
+        for (int64_t k = k0; k <= k1; ++k)
+            for (int64_t j = j0; j <= j1; ++j)
+                for (int64_t i = i0; i <= i1; ++i) {
+                    const int64_t ii = i % n0, jj = j % n1, kk = k % n2;
+                    const float *p = pos + 3 * (ii + n0 * (jj + n1 * kk));
+                    const double ref[3] = {rx, ry, rz};
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        double d = (double)p[a] - ref[a];
+                        d -= (d >= 0.5 * box) ? box : ((d < -0.5 * box) ? -box : 0.0);
+                        lo[a] = fmin(lo[a], ref[a] + d);
+                        hi[a] = fmax(hi[a], ref[a] + d);
+                    }
+                }
+        double *o = boxes + 7 * b;
+        for (int a = 0; a < 3; ++a) {
+            o[a] = lo[a];
+            o[3 + a] = hi[a];
+        }
+        o[6] = 6.0 * (double)((i1 - i0) * (j1 - j0) * (k1 - k0));  // tetrahedra of the subblock
+    }
+}
+
+// overlap length of [lo, hi] with [x0, x1] over the periodic images of the interval
+__device__ __forceinline__ double overlap_1d(double lo, double hi, double x0, double x1, double box)
+{
+    double len = 0.0;
+#pragma unroll
+    for (int sgn = -1; sgn <= 1; ++sgn) {
+        const double a = fmax(lo + sgn * box, x0), b = fmin(hi + sgn * box, x1);
+        len += fmax(b - a, 0.0);
+    }
+    return len;
+}
+
+// one block per node of `nodes` (level, ix, iy, iz): estimated tetrahedra overlapping it
+__global__ void __launch_bounds__(256) k_node_counts(const double *__restrict__ boxes, int64_t nb,
+                                                     const int32_t *__restrict__ nodes, double box,
+                                                     double *__restrict__ counts)
+{
+    __shared__ double part[256];
+    const int32_t *nd = nodes + 4 * blockIdx.x;
+    const double size = box / (double)(1 << nd[0]);
+    const double x0 = nd[1] * size, y0 = nd[2] * size, z0 = nd[3] * size;
+    double sum = 0.0;
+    for (int64_t b = threadIdx.x; b < nb; b += blockDim.x) {
+        const double *o = boxes + 7 * b;
+        const double vx = o[3] - o[0], vy = o[4] - o[1], vz = o[5] - o[2];
+        const double vol = vx * vy * vz;
+        if (!(vol > 0.0)) continue;
+        const double ov = overlap_1d(o[0], o[3], x0, x0 + size, box) * overlap_1d(o[1], o[4], y0, y0 + size, box) *
+                          overlap_1d(o[2], o[5], z0, z0 + size, box);
+        sum += o[6] * ov / vol;
+    }
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counts[blockIdx.x] = part[0];
+}
+}  // namespace
+
+cudaError_t launch_subblock_boxes(const float *pos, const int64_t n[3], int s, double box, double *boxes,
+                                  cudaStream_t st)
+{
+    const int64_t nb = ((n[0] + s - 1) / s) * ((n[1] + s - 1) / s) * ((n[2] + s - 1) / s);
+    int64_t blocks = (nb + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks < 1) blocks = 1;
+    k_subblock_boxes<<<(unsigned)blocks, 256, 0, st>>>(pos, n[0], n[1], n[2], s, box, boxes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_node_counts(const double *boxes, int64_t nb, const int32_t *nodes, int64_t n_nodes, double box,
+                               double *counts, cudaStream_t st)
+{
+    if (n_nodes < 1) return cudaSuccess;
+    k_node_counts<<<(unsigned)n_nodes, 256, 0, st>>>(boxes, nb, nodes, box, counts);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStream_t st)
 {
     const int threads = 256;

@@ -224,3 +224,17 @@ def test_restriction_equals_coarse_uniform_deposits():
                     r = ref[z * bc:(z + 1) * bc, y * bc:(y + 1) * bc, x * bc:(x + 1) * bc]
                     assert np.max(np.abs(blk - r) / np.maximum(r, floor)) <= 1e-9, (l, x, y, z)
         row += nn ** 3
+
+
+def test_count_rule_build_matches_oracle():
+    """The paper's count criterion on the GPU against the float64 restatement: identical
+    leaves wherever no node's estimate lies within 1e-9 of the threshold."""
+    n, bc, ml = 16, 4, 4
+    for seed, thr in ((3, 600.0), (4, 100.0)):
+        pos = squeezed_lattice(n, seed=seed)
+        exp, est = oracle.build_octree_count(pos, n, bc, ml, count_threshold=thr, subblock=4)
+        near = [k for k, v in est.items() if abs(v - thr) <= 1e-9 * thr]
+        got = pse.build_octree_count(torch.from_numpy(pos).cuda(), n, bc, ml, thr, subblock=4).leaves()
+        assert not near
+        np.testing.assert_array_equal(got, exp)
+        assert len(set(exp[:, 0].tolist())) > 1  # the squeezed region refines deeper

@@ -110,3 +110,27 @@ def test_bad_leaf_sets_are_rejected():
         oracle.deposit_octree(pos, 4, np.array([[1, 0, 0, 0]], np.int32), 4, 1)  # does not tile
     with pytest.raises(RuntimeError):
         oracle.deposit_octree(pos, 4, np.array([[0, 0, 0, 0], [1, 0, 0, 0]], np.int32), 4, 1)  # overlaps
+
+
+# ------------------------------------------------------------- count criterion (Sec. 4) --
+def test_count_rule_root_estimate_is_every_tetrahedron():
+    """Every subblock box lies inside the periodic root, so the root's estimate is 6 n^3."""
+    n = 16
+    pos = zeldovich_positions(n, -2.0, 1.0, seed=5)
+    _, est = oracle.build_octree_count(pos, n, 4, 2, count_threshold=1e30, subblock=4)
+    assert est[(0, 0, 0, 0)] == pytest.approx(6 * n ** 3, rel=1e-12)
+
+
+@pytest.mark.parametrize("thr", [6 * 16 ** 3 / 8 - 1, 6 * 16 ** 3 / 64 - 1, 6 * 16 ** 3 / 64 + 1])
+def test_count_rule_undisplaced_lattice_closed_form(thr):
+    """Undisplaced lattice: the subblock boxes tile the box, so a node at level l is
+    estimated at 6 n^3 / 8^l and the tree refines uniformly while that exceeds the threshold."""
+    n, ml = 16, 4
+    leaves, est = oracle.build_octree_count(lattice_positions(n), n, 4, ml, count_threshold=thr, subblock=4)
+    for (l, x, y, z), v in est.items():
+        assert v == pytest.approx(6 * n ** 3 / 8 ** l, rel=1e-12)
+    lev = 0
+    while lev < ml and 6 * n ** 3 / 8 ** lev > thr:
+        lev += 1
+    assert set(leaves[:, 0].tolist()) == {lev}
+    assert len(leaves) == 8 ** lev
