@@ -36,9 +36,10 @@ UNIT = "tets/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
 # Algorithmic work per unit for the ALU roofline of the warp-cooperative kernel
-# (FP32-pipe floating-point operations, FMA = 2).  Derivation in the design doc
-# ("Roofline"): per tetrahedron set-up, per bounding-box cell classification,
-# per partial clip.
+# (FP32 floating-point operations, FMA = 2): per tetrahedron the determinant, bounding
+# box and face planes (~150); per bounding-box cell one classification against 4 planes
+# (~32); per partial clip the intersections and fan integrals of the face polygons
+# against the cell's slabs (~620).
 FLOP_PER_TET = 150.0
 FLOP_PER_BBOX_CELL = 32.0
 FLOP_PER_CLIP = 620.0

@@ -23,7 +23,7 @@
  *  - Positions: float32 [n0*n1*n2][3], particle (i,j,k) at flat index
  *    i + n0*(j + n1*k) (x fastest: the particle IDs' Lagrangian order, Sec. 3).
  *  - Tessellation: the Kuhn split of each Lagrangian cube around its 000-111
- *    diagonal (the paper uses "6 tetrahedra" without fixing which, Sec. 2):
+ *    diagonal (the paper cuts each cube into six tetrahedra without fixing which, Sec. 2):
  *    tetrahedron s (0..5) of cube (i,j,k) visits corners 000, e_a, e_a+e_b, 111
  *    for the axis permutation (a,b,c) = xyz, xzy, yxz, yzx, zxy, zyx.
  *    Its id is 6*cube + s, with cube = i + n0*(j + n1*k) (periodic lattices)

@@ -548,7 +548,7 @@ double oracle_tet_volume(const double *tet12)
  * tracers' bounding box).  A node at level l has side box/2^l and, if it is a
  * leaf, carries a block of bc^3 cells of side h_l = box/(bc*2^l) (every leaf has
  * the same cell count, Sec. 4).  Reading of the refinement rule used here (the
- * paper refines on an overlap count; this build refines on tetrahedron size): a
+ * paper refines on an overlap count; this rule refines on tetrahedron size): a
  * node is refined iff l < max_level and the median, over the tetrahedra whose
  * vertex centroid lies in the node, of the tetrahedron's mean edge length is
  * below threshold_cells * h_l.  A node without tetrahedra is a leaf.  The median

@@ -3,7 +3,7 @@
 Every translation unit under csrc/ is compiled in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3`` and linked into
 ``paper_1612_09491_gb300/_build/libpse.so`` (the CUDA runtime is linked
-statically, so the library needs only the driver at run time).
+statically, so the library needs only the CUDA driver at run time).
 """
 from __future__ import annotations
 
