@@ -63,7 +63,7 @@ extern "C" {
 #define PSE_ERR_CUDA -2        /* a CUDA runtime call failed (message in pse_last_error) */
 #define PSE_ERR_OOM -3         /* the library could not allocate device or host memory */
 #define PSE_ERR_TIMEOUT -4     /* a bounded device-side wait ran out (spin_limit) */
-#define PSE_ERR_UNSUPPORTED -5 /* a valid request this build does not implement */
+#define PSE_ERR_UNSUPPORTED -5 /* a valid request the library does not implement */
 #define PSE_ERR_WORKSPACE -6   /* ws_bytes smaller than pse_workspace_size() */
 #define PSE_ERR_DEVICE -7      /* a device-side check failed (e.g. a tetrahedron wider than box/2) */
 
