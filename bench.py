@@ -482,6 +482,12 @@ def main():
     def step(accumulate=False):
         call(tuned, accumulate=accumulate)
 
+    # the workload's tetrahedron sizes (mean edge length in cells), from the cost-model features
+    from paper_1612_09491_gb300 import costmodel as cm
+    edges = cm.features(pos, n, g)[:, 11].cpu().numpy()
+    tet_sizes = {"mean_edge_cells_quantiles": dict(zip(("min", "p01", "median", "p99", "max"),
+                                                       [float(v) for v in np.quantile(edges, [0, .01, .5, .99, 1])]))}
+    del edges
     # kernels of one step: [bin pass, chunk scan,] deposit kernel, mass renormalisation
     launches_per_step = 4 if tuned["schedule"] == "binned" else 2
     # counters of one pass (synchronising call, outside the timed region)
@@ -591,7 +597,8 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "clips_per_s": clips_per_s,
             "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
-                                            "degenerate_tets", "single_cell_tets")},
+                                            "degenerate_tets", "single_cell_tets", "inverted_tets", "bin_counts")},
+            "tet_sizes": tet_sizes,
             "fp64_gpu_baseline": base,
             "error_vs_oracle": oracle_err,
             "kernel_ms": kern_ms,

@@ -128,6 +128,9 @@ typedef struct pse_deposit_stats {
     uint64_t bin_counts[8];    /* binned schedule: tetrahedra per size bin */
     double mass_in;            /* sum of m_t over the processed tetrahedra */
     double mass_dropped;       /* open grids: mass that fell outside the grid */
+    uint64_t inverted_tets;    /* lattice tetrahedra turned inside out by shell crossing: signed volume of
+                                  the other sign than in the Lagrangian lattice (they deposit positive
+                                  mass, Sec. 2); explicit tetrahedra: negative signed volume */
 } pse_deposit_stats;
 
 /*

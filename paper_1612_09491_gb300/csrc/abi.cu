@@ -398,6 +398,7 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
         for (int b = 0; b < 8; ++b) h_stats->bin_counts[b] = hw.stats[pse::ST_BIN0 + b];
         h_stats->mass_in = hw.mass_in;
         h_stats->mass_dropped = hw.mass_dropped;
+        h_stats->inverted_tets = hw.stats[pse::ST_INVERTED];
         if (hw.error_code != 0)
             return fail(PSE_ERR_DEVICE,
                         hw.error_code == 1 ? "a tetrahedron is wider than the periodic grid (detail %d)"

@@ -23,6 +23,12 @@ __device__ __forceinline__ void kuhn_offsets(int s, int (&o1)[3], int (&o2)[3])
     }
 }
 
+// The Lagrangian orientation of Kuhn tetrahedron s is the parity of its axis permutation:
+// xzy, yxz and zyx are odd, so those tetrahedra start with a negative signed volume.  A
+// tetrahedron is inverted (turned inside out by shell crossing) when its signed volume
+// now has the other sign.
+__device__ __forceinline__ bool kuhn_negative(int s) { return s == 1 || s == 2 || s == 5; }
+
 // floor to int for coordinates in grid units; non-finite or out-of-range values map to
 // kBadCoord, which tet_ok() rejects before anything is indexed with them.
 constexpr int kBadCoord = -(1 << 30);

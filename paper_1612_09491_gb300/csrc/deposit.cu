@@ -50,8 +50,13 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
             m_t = P.m_tet;
         }
         TetSetup<T> ts;
-        if (tet_setup<T>(v, ts)) swap12(res);
-        if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+        const bool negative = tet_setup<T>(v, ts);
+        if (negative) swap12(res);
+        if (STATS) {
+            cnt.u[ST_TETS]++;
+            cnt.mass_in += m_t;
+            cnt.u[ST_INVERTED] += (negative != (P.src != SRC_TETS && kuhn_negative((int)(t % 6)))) ? 1 : 0;
+        }
         if (!tet_ok(base, ts)) {
             set_error(P.ws, 4, (int)(t & 0x7fffffff));
             continue;
@@ -245,7 +250,11 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                 }
                 TetSetup<float> ts;
                 const bool swapped = tet_setup<float>(v, ts);
-                if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+                if (STATS) {
+                    cnt.u[ST_TETS]++;
+                    cnt.mass_in += m_t;
+                    cnt.u[ST_INVERTED] += (swapped != (P.src != SRC_TETS && kuhn_negative(s))) ? 1 : 0;
+                }
                 const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
                 if (!tet_ok(base, ts)) {
                     set_error(P.ws, 4, lane);
@@ -338,8 +347,13 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
             }
             if (ok) {
                 TetSetup<float> ts;
-                if (tet_setup<float>(v, ts)) swap12(res);
-                if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+                const bool negative = tet_setup<float>(v, ts);
+                if (negative) swap12(res);
+                if (STATS) {
+                    cnt.u[ST_TETS]++;
+                    cnt.mass_in += m_t;
+                    cnt.u[ST_INVERTED] += (negative != (P.src != SRC_TETS && kuhn_negative((int)(t % 6)))) ? 1 : 0;
+                }
                 const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
                 if (!tet_ok(base, ts)) {
                     set_error(P.ws, 4, (int)(t & 0x7fffffff));

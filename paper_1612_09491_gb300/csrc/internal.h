@@ -19,6 +19,7 @@ enum StatSlot : int32_t {
     ST_FP64_REDOS,
     ST_DEGENERATE,
     ST_SINGLE_CELL,
+    ST_INVERTED,  // tetrahedra whose orientation differs from the Lagrangian one (shell crossing)
     ST_BIN0,  // 8 bins
     ST_NUM_U64 = ST_BIN0 + 8
 };

@@ -231,7 +231,11 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
         int k[4][3];
         lattice_tet_raw(P, ci, cj, ck, (int)(t % 6), x, k);
         const double m_t = P.m_tet;
-        if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+        if (STATS) {
+            cnt.u[ST_TETS]++;
+            cnt.mass_in += m_t;
+            cnt.u[ST_INVERTED] += ((det6_box(P, x, k) < 0.0) != kuhn_negative((int)(t % 6))) ? 1 : 0;
+        }
         cnt.tgt += m_t;
         double cen[3];
         tet_centroid(P, x, k, cen);
@@ -366,7 +370,11 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
             if (have) {
                 lattice_tet_raw(P, ci, cj, ck, s, x, k);
                 tet_centroid(P, x, k, cen);
-                if (STATS) { cnt.u[ST_TETS]++; cnt.mass_in += m_t; }
+                if (STATS) {
+            cnt.u[ST_TETS]++;
+            cnt.mass_in += m_t;
+            cnt.u[ST_INVERTED] += ((det6_box(P, x, k) < 0.0) != kuhn_negative(s)) ? 1 : 0;
+        }
                 cnt.tgt += m_t;
                 if (det6_box(P, x, k) == 0.0) {
                     add_mass(P, cen, m_t, cnt, STATS);

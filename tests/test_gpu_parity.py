@@ -481,3 +481,16 @@ def test_config2_fp32_vs_fp64_gpu_all_cells():
     e = cell_errors(a, b)
     assert e["max_rel"] <= TOL32, e
     assert e["mass"] <= MASS32, e
+
+
+def test_inverted_tetrahedra_are_counted_alike_by_every_schedule():
+    """Shell crossing turns tetrahedra inside out; every schedule counts the same ones (an
+    undisplaced lattice has none)."""
+    n, g = 16, 48
+    counts = set()
+    for name, prec, sched in PATHS:
+        _, st = gpu_lattice(zeldovich_positions(n, -1.5, 3.0, seed=77), n, g, prec, sched, stats=True)
+        counts.add(st["inverted_tets"])
+    assert len(counts) == 1 and counts.pop() > 0
+    _, st = pse.deposit_uniform(dev(lattice_positions(8)), 8, 16, stats=True)
+    assert st["inverted_tets"] == 0
