@@ -95,3 +95,89 @@ def test_streamed_rejects():
         pse.deposit_uniform_streamed(pos, 8, 8, 0)  # slab_cubes < 1
     with pytest.raises(pse.PseError):
         pse.deposit_uniform_streamed(pos, 8, 8, 2, tuning={"use_graph": 1}, schedule=pse.PSE_BINNED_PERSISTENT)
+
+
+def _max_displacement(pos, n):
+    """Largest |x - q| per axis over the lattice, nearest periodic image (positions on the GPU)."""
+    p = pos.view(n, n, n, 3)
+    q = torch.arange(n, device=pos.device, dtype=torch.float32) / n
+    out = 0.0
+    for a, shape in enumerate(((1, 1, n), (1, n, 1), (n, 1, 1))):
+        d = p[..., a] - q.view(*shape)
+        d -= torch.round(d)
+        out = max(out, float(d.abs().max()))
+    return out
+
+
+def _cubes_reaching(posh, n, cell, g, psi_max):
+    """Cubes whose corner bounding box (corners taken at the image nearest corner 0) touches `cell`
+    of a periodic g^3 grid: the Lagrangian window that displacements up to psi_max allow, then
+    the exact box test on the cubes of that window."""
+    h = 1.0 / n
+    ax = []
+    for a in range(3):
+        lo = int(np.floor((cell[a] / g - h - psi_max) * n)) - 1
+        hi = int(np.ceil(((cell[a] + 1) / g + psi_max) * n)) + 1
+        ax.append(np.unique(np.arange(lo, hi + 1) % n))
+    kk, jj, ii = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    p0 = posh[ii + n * (jj + n * kk)].astype(np.float64)
+    lo = p0.copy()
+    hi = p0.copy()
+    for dz in (0, 1):
+        for dy in (0, 1):
+            for dx in (0, 1):
+                c = posh[(ii + dx) % n + n * ((jj + dy) % n + n * ((kk + dz) % n))].astype(np.float64)
+                d = c - p0
+                d -= np.floor(d + 0.5)
+                lo = np.minimum(lo, p0 + d)
+                hi = np.maximum(hi, p0 + d)
+    blo = np.floor(lo * g).astype(np.int64)
+    ext = np.floor(hi * g).astype(np.int64) - blo
+    sel = np.all(np.mod(np.asarray(cell) - blo, g) <= ext, axis=1)
+    return (ii + n * (jj + n * kk))[sel]
+
+
+def test_config5_streamed_full_size_sampled_cells():
+    """1024^3 particles (6.4B tetrahedra), k^-2, rms 3 spacings, streamed from pinned host memory in
+    z-slabs of 64 cube layers onto the octree of 128^3-cell blocks, levels 0-4 (2048^3 finest), in
+    the bench's launch configuration: the whole deposit conserves mass and counts every
+    tetrahedron; 6 random leaf cells match the oracle's exact overlaps (FP64) of every
+    tetrahedron that can reach them."""
+    from pse_inputs import zeldovich_positions_device
+    cfg = CONFIGS[5]
+    n, bc = cfg.n, cfg.bc
+    pos = zeldovich_positions_device(n, cfg.spectral_index, cfg.rms_disp, cfg.seed, device="cuda")
+    psi_max = _max_displacement(pos, n) + 1.0 / n
+    h = torch.empty((n ** 3, 3), dtype=torch.float32).pin_memory()
+    h.copy_(pos)
+    del pos
+    torch.cuda.empty_cache()
+    oct_ = pse.build_octree_streamed(h, n, bc, cfg.max_level, 64, 2.0)
+    leaves = oct_.leaves()
+    assert sum(8.0 ** -int(l) for l in leaves[:, 0]) == pytest.approx(1.0, abs=1e-12)
+    out, st = pse.deposit_octree_streamed(h, n, oct_, 64, stats=True, tuning={"blocks_per_sm": 3})
+    assert st["tets"] == cfg.n_tets
+    assert abs(float(out.sum()) - 1.0) <= 1e-12
+    posh = h.numpy()
+    mt = 1.0 / (6 * n ** 3)
+    rng = np.random.default_rng(55)
+    for _ in range(6):
+        li = int(rng.integers(0, len(leaves)))
+        lvl, lx, ly, lz = (int(v) for v in leaves[li])
+        cx, cy, cz = (int(v) for v in rng.integers(0, bc, 3))
+        g = bc << lvl
+        cell = np.array([lx * bc + cx, ly * bc + cy, lz * bc + cz])
+        got = float(out[li, cz, cy, cx])
+        exp = 0.0
+        for c in _cubes_reaching(posh, n, cell, g, psi_max):
+            for s in range(6):
+                tet = oracle.lattice_tet(posh, n, int(c), s)
+                vol = oracle.tet_volume(tet)
+                if vol == 0.0:  # degenerate: all its mass goes to the cell of the vertex centroid
+                    exp += mt * bool(np.all(np.mod(np.floor(tet.mean(0) * g), g) == cell))
+                    continue
+                cells, vols = oracle.tet_cells(tet, np.full(3, 1.0 / g))
+                hit = np.all(np.mod(cells, g) == cell, axis=1)
+                exp += mt * vols[hit].sum() / vol
+        assert abs(got - exp) <= 1e-5 * max(exp, 1e-3 / g ** 3), (cell, lvl, got, exp)
