@@ -47,8 +47,8 @@ FLOP_PER_CLIP = 620.0
 # per SM) on the headline workload: DRAM bytes read + written per launch, and thread
 # instructions issued per partial clip (warp instructions x active lanes / partial clips).
 # Both go stale when the kernel changes and must be re-taken with it.
-DRAM_BYTES_PER_LAUNCH = 256_682_496
-THREAD_INST_PER_CLIP = 4803.5
+DRAM_BYTES_PER_LAUNCH = 254_682_368
+THREAD_INST_PER_CLIP = 4803.4
 SM_COUNT_GB300 = 152
 PRECISION = "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up"
 FP32_LANES_PER_SM = 128
@@ -227,6 +227,31 @@ def _timed(step, steps, warmup, flush, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def _tet_size_sample(pos, n, g, layers=8):
+    """Quantiles of the tetrahedra's mean edge length in cells of a g^3 grid, from the cost-model
+    features of `layers` cube layers in the middle of the lattice.  The rows are moved to the
+    periodic image nearest their Lagrangian sites and deposited as an open lattice, so no
+    tetrahedron of the sample wraps."""
+    import numpy as np
+    import torch
+    k0 = n // 2
+    rows = pos[k0 * n * n:(k0 + layers + 1) * n * n].to("cuda", non_blocking=False).view(layers + 1, n, n, 3)
+    ax = torch.arange(n, device=rows.device, dtype=torch.float32) / n
+    q = torch.stack(torch.broadcast_tensors(ax.view(1, 1, n),
+                                            ax.view(1, n, 1),
+                                            ((k0 + torch.arange(layers + 1, device=rows.device)) / n)
+                                            .float().view(layers + 1, 1, 1)), -1)
+    d = rows - q
+    d -= torch.round(d)
+    x = (q + d).reshape(-1, 3).contiguous()
+    from paper_1612_09491_gb300 import costmodel as cm
+    e = cm.features(x, (n, n, layers + 1), g, periodic=False)[:, 11]
+    e = e[:: max(1, e.numel() // 4_000_000)].cpu().numpy()
+    return {"mean_edge_cells_quantiles": dict(zip(("min", "p01", "median", "p99", "max"),
+                                                  [float(v) for v in np.quantile(e, [0, .01, .5, .99, 1])])),
+            "sample": f"{layers} cube layers in the middle of the lattice, cells of the {g}^3 grid"}
+
+
 def run_workload(args, cfg):
     """Workloads 3 (octree), 4 (uniform 512^3 with the learned cost model) and 5 (octree over a
     1024^3 lattice streamed from pinned host memory in z-slabs).  One JSON line, like main()."""
@@ -357,6 +382,7 @@ def run_workload(args, cfg):
                 "note": "the block's fringe holds slivers of single tetrahedra; 'filled' = FP64 mass >= half "
                         "the mean cell mass"}
 
+    tet_sizes = _tet_size_sample(h if cfg.index == 5 else pos, n, cfg.grid_n)
     with ClockSampler(bus_id_of(0)) as clk:
         t_wall0 = time.perf_counter()
         step_ms = _timed(step, args.steps, args.warmup, flush, stream)
@@ -407,7 +433,8 @@ def run_workload(args, cfg):
         "data": "synthetic", "config": config,
         "clips_per_s": st["partial_clips"] / (ms * 1e-3),
         "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
-                                        "degenerate_tets", "single_cell_tets")},
+                                        "degenerate_tets", "single_cell_tets", "inverted_tets")},
+        "tet_sizes": tet_sizes,
         "mass_error": mass_error,
         "fp64_gpu_baseline": base,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
@@ -555,7 +582,8 @@ def main():
             bev[1].record(stream)
             torch.cuda.synchronize()
             bms = bev[0].elapsed_time(bev[1])
-            err = cell_errors(fast_grid, out.cpu().numpy())
+            ref64 = out.cpu().numpy()
+            err = cell_errors(fast_grid, ref64)
             base = {"tets_per_s": n_tets / (bms * 1e-3), "ms_per_step": bms, "speedup": (n_tets / (ms * 1e-3)) /
                     (n_tets / (bms * 1e-3)), "error_of_timed_arm": err}
             # the paper's GPU design (one warp per tetrahedron, Sec. 6.2) with the same clip
@@ -564,6 +592,14 @@ def main():
             pms = sum(pms) / len(pms)
             base["paper_design_warp_per_tet"] = {"tets_per_s": n_tets / (pms * 1e-3), "ms_per_step": pms,
                                                  "speedup_of_timed_arm": pms / ms}
+            # the same clips with compensated FP32 (hi, lo) accumulation instead of FP64 reductions
+            knobs = {k: v for k, v in tuned.items() if k != "schedule"}
+            csched = pse.PSE_BINNED_PERSISTENT if tuned["schedule"] == "binned" else pse.PSE_WARP_COOPERATIVE
+            cms = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, tuning=knobs, schedule=csched,
+                                                     precision=pse.PSE_FP32_COMPENSATED), 3, 1, flush, stream)
+            cms = sum(cms) / len(cms)
+            base["fp32_compensated_accumulation"] = {"tets_per_s": n_tets / (cms * 1e-3), "ms_per_step": cms,
+                                                     "error_vs_fp64": cell_errors(out.cpu().numpy(), ref64)}
         # roofline of the dominant kernel (FP32 ALU bound)
         alg_flop = (FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] +
                     FLOP_PER_CLIP * st["partial_clips"])

@@ -70,6 +70,10 @@ extern "C" {
 /* precision (pse_deposit_opts.precision) */
 #define PSE_FP64_PLAIN 0   /* every step in float64 */
 #define PSE_FP32_FP64ACC 1 /* float32 clip with float64 redo of guarded clips; float64 accumulation */
+#define PSE_FP32_COMPENSATED 2 /* the float32 clip of PSE_FP32_FP64ACC; each cell sums its deposits as a
+                                  float32 pair (hi, lo) with an error-free two-sum on every add, held in
+                                  the cell's own 8 output bytes and turned into float64 hi + lo at the
+                                  end of the call (needs accumulate = 0) */
 
 /* schedule (pse_deposit_opts.schedule) */
 #define PSE_THREAD_PER_TET 0    /* one thread per tetrahedron (the plain baseline) */
@@ -98,7 +102,7 @@ typedef struct pse_lattice {
 } pse_lattice;
 
 typedef struct pse_deposit_opts {
-    int32_t precision;       /* PSE_FP64_PLAIN or PSE_FP32_FP64ACC */
+    int32_t precision;       /* PSE_FP64_PLAIN, PSE_FP32_FP64ACC or PSE_FP32_COMPENSATED */
     int32_t schedule;        /* PSE_THREAD_PER_TET, PSE_WARP_COOPERATIVE or PSE_BINNED_PERSISTENT */
     const void *cost_model;  /* nullable device cost model (pse_costmodel_*): the binned schedule then splits
                                 the tetrahedra whose predicted partial clips exceed split_cells, instead

@@ -12,6 +12,7 @@ import ctypes
 from . import _lib
 from ._lib import (  # noqa: F401
     PSE_BINNED_PERSISTENT,
+    PSE_FP32_COMPENSATED,
     PSE_FP32_FP64ACC,
     PSE_FP64_PLAIN,
     PSE_THREAD_PER_TET,

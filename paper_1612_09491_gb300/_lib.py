@@ -24,6 +24,7 @@ PSE_ERR_DEVICE = -7
 
 PSE_FP64_PLAIN = 0
 PSE_FP32_FP64ACC = 1
+PSE_FP32_COMPENSATED = 2
 PSE_THREAD_PER_TET = 0
 PSE_WARP_COOPERATIVE = 1
 PSE_BINNED_PERSISTENT = 2

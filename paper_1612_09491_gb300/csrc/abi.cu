@@ -136,8 +136,10 @@ int check_grid(const int64_t grid_n[3], int64_t &cells)
 
 int check_opts(const pse_deposit_opts &o)
 {
-    if (o.precision != PSE_FP64_PLAIN && o.precision != PSE_FP32_FP64ACC)
+    if (o.precision != PSE_FP64_PLAIN && o.precision != PSE_FP32_FP64ACC && o.precision != PSE_FP32_COMPENSATED)
         return fail(PSE_ERR_INVALID_ARG, "unknown precision %d", o.precision);
+    if (o.precision == PSE_FP32_COMPENSATED && o.accumulate)
+        return fail(PSE_ERR_UNSUPPORTED, "compensated FP32 accumulation overwrites its output (accumulate = 0)");
     if (o.schedule != PSE_THREAD_PER_TET && o.schedule != PSE_WARP_COOPERATIVE && o.schedule != PSE_BINNED_PERSISTENT &&
         o.schedule != PSE_WARP_PER_TET)
         return fail(PSE_ERR_INVALID_ARG, "unknown schedule %d", o.schedule);
@@ -277,6 +279,8 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
     // it needs the output to hold this call's deposits only (accumulate = 0)
     const bool renorm = o.mass_fixup && !o.accumulate && o.precision != PSE_FP64_PLAIN;
     p.fixup = renorm ? 1 : 0;
+    const bool comp = o.precision == PSE_FP32_COMPENSATED;
+    p.comp = comp ? 1 : 0;
     const int bps = (tu && tu->blocks_per_sm > 0) ? tu->blocks_per_sm : kDefaultBlocksPerSm;
     if (p.n_units > 0 && o.schedule != PSE_THREAD_PER_TET)
         p.n_items = (p.src == pse::SRC_LATTICE) ? ((p.nc[0] + 31) / 32) * p.nc[1] * p.nc[2] : (p.n_units + 31) / 32;
@@ -327,9 +331,9 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
             });
         }
         if (r != PSE_OK) return r;
-        if (renorm && p.n_units > 0) {
-            e = pse::launch_scale(p.out, cells, p.ws, s);
-            if (e != cudaSuccess) return cuda_fail(e, "mass renormalisation launch");
+        if ((renorm || comp) && p.n_units > 0) {
+            e = pse::launch_finish(p.out, cells, p.ws, comp, renorm, s);
+            if (e != cudaSuccess) return cuda_fail(e, "deposit finish launch");
         }
         return PSE_OK;
     };

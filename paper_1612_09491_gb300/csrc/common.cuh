@@ -192,8 +192,46 @@ __device__ __forceinline__ int64_t fold_cell(int64_t c, int64_t g)
     return c < 0 ? c + g : c;
 }
 
+// How a kernel adds to the output cells (compile-time, so that the FP64 kernels carry
+// no trace of the other mode):
+//  * F64: one global FP64 reduction per addend.
+//  * COMP: compensated FP32 accumulation.  Until the end of the call each cell holds an
+//    FP32 pair (hi at the lower 4 bytes, lo at the upper 4).  hi takes m rounded to float
+//    with an atomic add that returns the previous value; the exact rounding error of that
+//    add (Knuth's two-sum, exact under round-to-nearest) and the error of rounding m to
+//    float go to lo.  hi + lo then carries the cell's sum to about 2^-48 relative per addend.
+//  * RUNTIME: either, from P.comp (the baseline kernels).
+enum class Acc : int { F64 = 0, COMP = 1, RUNTIME = 2 };
+
+__device__ __forceinline__ void cell_add_compensated(double *addr, double m)
+{
+    float *hl = reinterpret_cast<float *>(addr);
+    const float v = __double2float_rn(m);
+    const float r = __double2float_rn(m - (double)v);
+    const float old = atomicAdd(hl, v);
+    const float s = __fadd_rn(old, v);
+    const float bv = __fsub_rn(s, old);
+    const float e = __fadd_rn(__fsub_rn(old, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+    const float c = __fadd_rn(e, r);
+    if (c != 0.f) atomicAdd(hl + 1, c);
+}
+
+template <Acc A = Acc::RUNTIME>
+__device__ __forceinline__ void cell_add(const DepositParams &P, double *addr, double m)
+{
+    if constexpr (A == Acc::F64) {
+        atomicAdd(addr, m);
+    } else if constexpr (A == Acc::COMP) {
+        cell_add_compensated(addr, m);
+    } else {
+        if (P.comp) cell_add_compensated(addr, m);
+        else atomicAdd(addr, m);
+    }
+}
+
 // Add m to cell (cx, cy, cz) (unfolded grid indices); returns false if the cell is
 // outside an open grid (then the mass is dropped).
+template <Acc A = Acc::RUNTIME>
 __device__ __forceinline__ bool deposit_cell(const DepositParams &P, int64_t cx, int64_t cy, int64_t cz, double m)
 {
     if (P.periodic) {
@@ -203,7 +241,7 @@ __device__ __forceinline__ bool deposit_cell(const DepositParams &P, int64_t cx,
     } else if (cx < 0 || cy < 0 || cz < 0 || cx >= P.g[0] || cy >= P.g[1] || cz >= P.g[2]) {
         return false;
     }
-    atomicAdd(P.out + (cx + P.g[0] * (cy + P.g[1] * cz)), m);
+    cell_add<A>(P, P.out + (cx + P.g[0] * (cy + P.g[1] * cz)), m);
     return true;
 }
 
@@ -386,17 +424,17 @@ __device__ __forceinline__ void store_record(WarpSmem *S, int lane, const TetSet
 
 // Add m to cell (cx, cy, cz) (base-cell frame) of virtual tetrahedron t: the uniform
 // grid (folded / dropped as deposit_cell does) or t's octree leaf block.
-template <bool OCT>
+template <bool OCT, Acc A>
 __device__ __forceinline__ bool deposit_pair(const DepositParams &P, const WarpSmem *S, int t, int cx, int cy, int cz,
                                              double m)
 {
     if constexpr (OCT) {
         const int64_t bc = P.bc;
         const int64_t lx = cx - S->org[0][t], ly = cy - S->org[1][t], lz = cz - S->org[2][t];
-        atomicAdd(P.out + (int64_t)S->leaf[t] * bc * bc * bc + lx + bc * (ly + bc * lz), m);
+        cell_add<A>(P, P.out + (int64_t)S->leaf[t] * bc * bc * bc + lx + bc * (ly + bc * lz), m);
         return true;
     } else {
-        return deposit_cell(P, (int64_t)S->base[0][t] + cx, (int64_t)S->base[1][t] + cy, (int64_t)S->base[2][t] + cz,
+        return deposit_cell<A>(P, (int64_t)S->base[0][t] + cx, (int64_t)S->base[1][t] + cy, (int64_t)S->base[2][t] + cz,
                             m);
     }
 }
@@ -410,7 +448,7 @@ __device__ __forceinline__ void q_cell(const WarpSmem *S, unsigned long long ent
     cz = S->lo[2][t] + (int)((ent >> (5 + 2 * kQBits)) & kQMask);
 }
 
-template <bool STATS, bool OCT>
+template <bool STATS, bool OCT, Acc A>
 __device__ __forceinline__ void deposit_clip(const DepositParams &P, const WarpSmem *S, int t, int cx, int cy, int cz,
                                              double vol, Counters &cnt)
 {
@@ -418,12 +456,12 @@ __device__ __forceinline__ void deposit_clip(const DepositParams &P, const WarpS
     if (vol > 0.0) {
         const double m = (double)(S->rho[t] * (float)vol);
         cnt.dep += m;
-        if (!deposit_pair<OCT>(P, S, t, cx, cy, cz, m) && STATS) cnt.dropped += m;
+        if (!deposit_pair<OCT, A>(P, S, t, cx, cy, cz, m) && STATS) cnt.dropped += m;
     }
 }
 
 // FP32 clips of the first `count` entries of S->q (tetrahedra below the guard).
-template <bool STATS, bool OCT>
+template <bool STATS, bool OCT, Acc A>
 __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
 {
     if (lane < count) {
@@ -439,14 +477,14 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
         for (int f = 0; f < 4; ++f) n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
         float err;
         const double vol = (double)overlap_volume_ax<float>(p, n, S->axis[t], S->lx[t], S->ly[t], err);
-        deposit_clip<STATS, OCT>(P, S, t, cx, cy, cz, vol, cnt);
+        deposit_clip<STATS, OCT, A>(P, S, t, cx, cy, cz, vol, cnt);
     }
     __syncwarp();
 }
 
 // Float64 clips (exact vertices) of the first `count` entries of S->gq.  Guarded pairs
 // are queued apart so that these rounds run with full warps.
-template <bool STATS, bool OCT>
+template <bool STATS, bool OCT, Acc A>
 __device__ __forceinline__ void redo_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
 {
     if (lane < count) {
@@ -454,7 +492,7 @@ __device__ __forceinline__ void redo_round(const DepositParams &P, WarpSmem *S, 
         q_cell(S, S->gq[lane], t, cx, cy, cz);
         const double vol = redo_fp64(S, t, cx, cy, cz);
         if (STATS) cnt.u[ST_FP64_REDOS]++;
-        deposit_clip<STATS, OCT>(P, S, t, cx, cy, cz, vol, cnt);
+        deposit_clip<STATS, OCT, A>(P, S, t, cx, cy, cz, vol, cnt);
     }
     __syncwarp();
 }
@@ -462,7 +500,7 @@ __device__ __forceinline__ void redo_round(const DepositParams &P, WarpSmem *S, 
 // Enumerate every (virtual tetrahedron, cell) pair of the 32 records in S (npairs:
 // this lane's pair count), 32 pairs per round: classify; deposit "cell inside"
 // pairs; queue partial pairs and clip them 32 at a time.
-template <bool STATS, bool OCT>
+template <bool STATS, bool OCT, Acc A>
 __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, int lane, int npairs, Counters &cnt)
 {
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -505,7 +543,7 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                 if (cls == CELL_INSIDE) {
                     const double m = (double)S->rho[t];
                     cnt.dep += m;
-                    if (!deposit_pair<OCT>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) && STATS)
+                    if (!deposit_pair<OCT, A>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) && STATS)
                         cnt.dropped += m;
                     if (STATS) cnt.u[ST_INSIDE_CELLS]++;
                 } else if (cls == CELL_PARTIAL) {
@@ -525,14 +563,14 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
         const bool last = b0 + 32 >= total;
         if (qn >= 32 || (last && qn > 0)) {
             const int take = qn >= 32 ? 32 : qn;
-            clip_round<STATS, OCT>(P, S, take, lane, cnt);
+            clip_round<STATS, OCT, A>(P, S, take, lane, cnt);
             if (lane < qn - take) S->q[lane] = S->q[take + lane];
             qn -= take;
             __syncwarp();
         }
         if (gn >= 32 || (last && gn > 0)) {
             const int take = gn >= 32 ? 32 : gn;
-            redo_round<STATS, OCT>(P, S, take, lane, cnt);
+            redo_round<STATS, OCT, A>(P, S, take, lane, cnt);
             if (lane < gn - take) S->gq[lane] = S->gq[take + lane];
             gn -= take;
             __syncwarp();

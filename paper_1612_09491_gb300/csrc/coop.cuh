@@ -1,0 +1,225 @@
+// coop.cuh -- the warp-cooperative deposit kernel k_warp_coop and its launcher, templated
+// on the accumulation mode: deposit.cu instantiates the FP64-reduction kernels and
+// deposit_comp.cu the compensated-FP32 ones, so the two build in parallel.
+//
+// One warp takes a batch of 32 tetrahedra (32 Lagrangian cubes x one Kuhn permutation),
+// enumerates all their (tetrahedron, cell) pairs 32 at a time, classifies them in
+// lock-step, deposits "cell inside tetrahedron" pairs at once and compacts the partial
+// pairs into a per-warp queue; whenever 32 are queued every lane clips one (FP32, in
+// registers).  Tetrahedra whose conditioning estimate exceeds the guard are clipped in
+// FP64.  This is the role of the paper's warp-per-tetrahedron kernel with its
+// shared-memory buffer of partial cells (Sec. 6.2), generalised to batches of tetrahedra
+// so that small tetrahedra fill the warp too.
+#pragma once
+
+#include "common.cuh"
+
+namespace pse {
+namespace {
+
+// ---------------------------------------------------------------------------
+// warp-cooperative FP32 path
+// ---------------------------------------------------------------------------
+// Split work item `item` of the binned schedule: chunk [first, first + len) of the
+// bounding-box cells of one queued tetrahedron, set up by lane 0 as record 0.  Returns
+// the lane's pair count (len on lane 0, else 0).
+template <bool STATS>
+__device__ __forceinline__ int chunk_setup(const DepositParams &P, WarpSmem *S, int lane, int64_t item, int64_t q,
+                                           Counters &cnt)
+{
+    // queue entry e: the last with chunk_start[e] <= item
+    int64_t lo = 0, hi = q - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (P.chunk_start[mid] <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    const int64_t first = (item - P.chunk_start[lo]) * (int64_t)P.chunk_cells;
+    const int64_t ncell = P.q_cells[lo];
+    const int len = (int)min((int64_t)P.chunk_cells, ncell - first);
+    if (lane != 0 || len <= 0) return 0;
+    const int64_t id = P.q_tet[lo];
+    P3<float> v[4], res[4];
+    int base[3];
+    double m_t;
+    if (P.src == SRC_TETS) {
+        explicit_tet<float>(P, id, v, base, res);
+        m_t = P.tet_mass[id];
+    } else {
+        int64_t ci, cj, ck;
+        if (!cube_of_unit(P, id / 6, ci, cj, ck)) return 0;
+        lattice_tet<float>(P, ci, cj, ck, (int)(id % 6), v, base, res);
+        m_t = P.m_tet;
+    }
+    TetSetup<float> ts;
+    if (tet_setup<float>(v, ts)) swap12(res);
+    store_record(S, 0, ts, res, base, m_t, P.kappa_max, (int)first);
+    if (STATS) cnt.u[ST_BBOX_CELLS] += len;
+    return len;
+}
+
+constexpr int kCoopThreads = 128;
+
+template <bool STATS, int MINB, bool BINNED, Acc A>
+__global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    Counters cnt;
+    if (STATS) cnt.zero();
+    cnt.zero_mass();
+    const int nsub = (P.src == SRC_TETS) ? 1 : 6;
+    // binned schedule: items [0, n_chunks) are pieces of split tetrahedra (largest work
+    // first), the rest are the rows; tetrahedra the bin pass queued are skipped there
+    int64_t n_chunks = 0, q = 0;
+    bool split = false;
+    if (BINNED) {
+        split = P.ws->queue_overflow == 0;
+        n_chunks = split ? (int64_t)P.ws->n_chunk_items : 0;
+        q = split ? min((int64_t)P.ws->queue_count, P.q_cap) : 0;
+    }
+
+    for (;;) {
+        unsigned long long item = 0;
+        if (lane == 0) item = atomicAdd(&P.ws->work_counter, 1ull);
+        item = __shfl_sync(kFull, item, 0);
+        const bool is_chunk = BINNED && (int64_t)item < n_chunks;
+        if (!is_chunk) {
+            item -= (unsigned long long)n_chunks;
+            if ((int64_t)item >= P.n_items) break;
+        }
+
+        // the 32 units (cubes or tetrahedra) of this item
+        int64_t unit = -1;
+        int64_t ci = 0, cj = 0, ck = 0;
+        if (is_chunk) {
+            // nothing: chunk_setup below
+        } else if (P.src == SRC_LATTICE) {
+            // rows of 32 cubes along x
+            const int64_t segs = (P.nc[0] + 31) / 32;
+            const int64_t row = (int64_t)item / segs, seg = (int64_t)item % segs;
+            const int64_t i = seg * 32 + lane;
+            if (i < P.nc[0]) {
+                ci = i;
+                cj = row % P.nc[1];
+                ck = row / P.nc[1];
+                unit = 1;
+            }
+        } else {
+            const int64_t u = (int64_t)item * 32 + lane;
+            if (u < P.n_units) {
+                unit = u;
+                if (P.src == SRC_CUBE_LIST && !cube_of_unit(P, u, ci, cj, ck)) {
+                    set_error(P.ws, 3, (int)(u & 0x7fffffff));
+                    unit = -1;
+                }
+            }
+        }
+
+        const int nsub_item = is_chunk ? 1 : nsub;
+        for (int s = 0; s < nsub_item; ++s) {
+            // ---- 1. one tetrahedron per lane (or the queued tetrahedron's chunk on lane 0)
+            int npairs = 0;
+            double m_t = 0.0;
+            if (is_chunk) {
+                npairs = chunk_setup<STATS>(P, S, lane, (int64_t)item, q, cnt);
+                __syncwarp();
+            } else if (unit >= 0) {
+                P3<float> v[4];
+                int base[3];
+                // tetrahedron id as the bin pass numbers it
+                const int64_t tid = (P.src == SRC_TETS) ? unit
+                                    : 6 * ((P.src == SRC_LATTICE) ? ci + P.nc[0] * (cj + P.nc[1] * ck) : unit) + s;
+                if (P.src == SRC_TETS) {
+                    explicit_tet<float>(P, unit, v, base);
+                    m_t = P.tet_mass[unit];
+                } else {
+                    lattice_tet<float>(P, ci, cj, ck, s, v, base);
+                    m_t = P.m_tet;
+                }
+                TetSetup<float> ts;
+                const bool swapped = tet_setup<float>(v, ts);
+                if (STATS) {
+                    cnt.u[ST_TETS]++;
+                    cnt.mass_in += m_t;
+                    cnt.u[ST_INVERTED] += (swapped != (P.src != SRC_TETS && kuhn_negative(s))) ? 1 : 0;
+                }
+                const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
+                if (!tet_ok(base, ts)) {
+                    set_error(P.ws, 4, lane);
+                } else if (ts.vol6 == 0.0) {
+                    int c[3];
+                    centroid_cell(ts.v, c);
+                    if (!deposit_cell<A>(P, (int64_t)base[0] + c[0], (int64_t)base[1] + c[1], (int64_t)base[2] + c[2], m_t) &&
+                        STATS)
+                        cnt.dropped += m_t;
+                    cnt.tgt += m_t;
+                    cnt.dep += m_t;
+                    if (STATS) cnt.u[ST_DEGENERATE]++;
+                } else if (ncell == 1) {
+                    if (!deposit_cell<A>(P, (int64_t)base[0] + ts.lo[0], (int64_t)base[1] + ts.lo[1],
+                                      (int64_t)base[2] + ts.lo[2], m_t) && STATS)
+                        cnt.dropped += m_t;
+                    cnt.tgt += m_t;
+                    cnt.dep += m_t;
+                    if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
+                } else if (BINNED && split &&
+                           (P.model ? ((P.qbits[tid >> 5] >> (tid & 31)) & 1u) != 0
+                                    : (ncell > P.split_cells && ncell <= (int64_t)INT32_MAX))) {
+                    // queued by the bin pass: its cells are done by the split work items
+                    cnt.tgt += m_t;
+                    if (STATS) cnt.u[ST_BIN0 + size_bin(ncell)]++;
+                } else if (ncell > (int64_t)(1 << 25)) {
+                    set_error(P.ws, 2, lane);  // 32 x 2^25 pairs still fit the int32 scan
+                } else {
+                    npairs = (int)ncell;
+                    cnt.tgt += m_t;
+                    if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
+                    // the vertices' rounding residuals, needed only by guarded tetrahedra
+                    P3<float> res[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) res[q] = mk<float>(0.f, 0.f, 0.f);
+                    if (!(ts.kappa <= P.kappa_max)) {
+                        P3<float> v2[4];
+                        int b2[3];
+                        if (P.src == SRC_TETS) explicit_tet<float>(P, unit, v2, b2, res);
+                        else lattice_tet<float>(P, ci, cj, ck, s, v2, b2, res);
+                        if (swapped) swap12(res);
+                    }
+                    store_record(S, lane, ts, res, base, m_t, P.kappa_max, 0);
+                }
+            }
+            // ---- 2. pair enumeration and clips
+            coop_pairs<STATS, false, A>(P, S, lane, npairs, cnt);
+            __syncwarp();
+        }
+    }
+    if (STATS) cnt.flush(P.ws);
+    if (P.fixup) cnt.flush_mass(P.ws);
+}
+
+template <bool BINNED, Acc A>
+cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, int64_t max_items, cudaStream_t st)
+{
+    // blocks_per_sm resident blocks of 128 threads: 2 (255 registers per thread, 8 warps per
+    // SM), 3 (170 registers, 12 warps) or 4 (128 registers, 16 warps).  The counting
+    // variant (stats) is built for 2 only.
+    const int threads = kCoopThreads;
+    const size_t smem = sizeof(WarpSmem) * (threads / 32);
+    const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
+    const void *k = stats ? (const void *)k_warp_coop<true, 2, BINNED, A>
+                    : minb == 4 ? (const void *)k_warp_coop<false, 4, BINNED, A>
+                    : minb == 3 ? (const void *)k_warp_coop<false, 3, BINNED, A>
+                                : (const void *)k_warp_coop<false, 2, BINNED, A>;
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int blocks = persistent_blocks(k, threads, smem);
+    const int64_t need = (max_items + threads / 32 - 1) / (threads / 32);
+    if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
+    void *args[] = {const_cast<DepositParams *>(&p)};
+    return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
+}
+
+}  // namespace
+}  // namespace pse

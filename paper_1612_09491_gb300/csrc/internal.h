@@ -65,6 +65,7 @@ struct DepositParams {
     // numerics
     float kappa_max;           // FP32 path: tetrahedra with kappa above this clip in float64
     int32_t fixup;             // accumulate mass_target / mass_deposited for the renormalisation
+    int32_t comp;              // 1: compensated FP32 accumulation, out holds (hi, lo) float pairs
     // octree target (deposit onto leaf blocks)
     int32_t bc;                // cells per leaf block side
     int32_t max_level;
@@ -115,7 +116,11 @@ cudaError_t costmodel_get(const CostModelDev *m, float *h_params, float *h_grad,
 cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStream_t st);
 cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread_per_tet, bool stats,
                                   int blocks_per_sm, cudaStream_t st);
-cudaError_t launch_scale(double *out, int64_t n, const Workspace *ws, cudaStream_t st);
+// the warp-cooperative kernel with compensated FP32 accumulation (deposit_comp.cu)
+cudaError_t launch_coop_comp(const DepositParams &p, bool stats, int blocks_per_sm, bool binned, int64_t max_items,
+                             cudaStream_t st);
+// end of an FP32 deposit: FP32 pairs to FP64 (comp) and / or the mass renormalisation (scale)
+cudaError_t launch_finish(double *out, int64_t n, const Workspace *ws, bool comp, bool scale, cudaStream_t st);
 cudaError_t launch_subblock_boxes(const float *pos, const int64_t n[3], int s, double box, double *boxes,
                                   cudaStream_t st);
 cudaError_t launch_node_counts(const double *boxes, int64_t nb, const int32_t *nodes, int64_t n_nodes, double box,

@@ -200,12 +200,13 @@ __device__ __forceinline__ double det6_box(const DepositParams &P, const float (
            e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
 }
 
+template <Acc A = Acc::RUNTIME>
 __device__ __forceinline__ void add_mass(const DepositParams &P, const double (&c)[3], double m, Counters &cnt,
                                          bool stats)
 {
     bool ok;
     const int64_t idx = point_cell(P, c, ok);
-    if (ok) atomicAdd(P.out + idx, m);
+    if (ok) cell_add<A>(P, P.out + idx, m);
     else if (stats) cnt.dropped += m;
 }
 
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
                         if (vol > 0.0) {
                             const double m = rho * vol;
                             cnt.dep += m;
-                            atomicAdd(blk + (cx - org[0]) + bc * ((cy - org[1]) + bc * (cz - org[2])), m);
+                            cell_add(P, blk + (cx - org[0]) + bc * ((cy - org[1]) + bc * (cz - org[2])), m);
                         }
                     }
         }
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
 // ---------------------------------------------------------------------------
 // warp-cooperative FP32 path: per sub-batch, rounds of (tetrahedron, leaf) pairs
 // ---------------------------------------------------------------------------
-template <bool STATS, int MINB>
+template <bool STATS, int MINB, Acc A>
 __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
         }
                 cnt.tgt += m_t;
                 if (det6_box(P, x, k) == 0.0) {
-                    add_mass(P, cen, m_t, cnt, STATS);
+                    add_mass<A>(P, cen, m_t, cnt, STATS);
                     cnt.dep += m_t;
                     if (STATS) cnt.u[ST_DEGENERATE]++;
                 } else {
@@ -422,7 +423,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                             const int64_t ncell = (int64_t)dim[0] * dim[1] * dim[2];
                             if (ts.dim[0] == 1 && ts.dim[1] == 1 && ts.dim[2] == 1) {
                                 // whole tetrahedron inside one cell of this leaf
-                                atomicAdd(P.out + (int64_t)hit.leaf * bc * bc * bc + (lo[0] - S->org[0][lane]) +
+                                cell_add<A>(P, P.out + (int64_t)hit.leaf * bc * bc * bc + (lo[0] - S->org[0][lane]) +
                                               bc * ((lo[1] - S->org[1][lane]) + bc * (lo[2] - S->org[2][lane])),
                                           m_t);
                                 cnt.dep += m_t;
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                         }
                     }
                 }
-                coop_pairs<STATS, true>(P, S, lane, npairs, cnt);
+                coop_pairs<STATS, true, A>(P, S, lane, npairs, cnt);
                 __syncwarp();
             }
             __syncwarp();
@@ -751,10 +752,14 @@ cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread
     const int threads = 128;
     const size_t smem = sizeof(WarpSmem) * (threads / 32);
     const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
-    const void *k = stats ? (const void *)k_oct_warp<true, 2>
-                    : minb == 4 ? (const void *)k_oct_warp<false, 4>
-                    : minb == 3 ? (const void *)k_oct_warp<false, 3>
-                                : (const void *)k_oct_warp<false, 2>;
+    const void *k = p.comp ? (stats ? (const void *)k_oct_warp<true, 2, Acc::COMP>
+                              : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::COMP>
+                              : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::COMP>
+                                          : (const void *)k_oct_warp<false, 2, Acc::COMP>)
+                    : (stats ? (const void *)k_oct_warp<true, 2, Acc::F64>
+                       : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::F64>
+                       : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::F64>
+                                   : (const void *)k_oct_warp<false, 2, Acc::F64>);
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);

@@ -31,6 +31,36 @@ def test_header_declares_what_binding_lists():
     assert declared_symbols() == sorted(_lib.EXPORTED)
 
 
+def test_binding_constants_match_header():
+    """Every integer constant the binding mirrors has the header's value."""
+    defs = dict(re.findall(r"^#define\s+(PSE_\w+)\s+(-?\d+)\b", open(HEADER).read(), re.M))
+    mirrored = [k for k in defs if hasattr(_lib, k)]
+    for k in ("PSE_FP64_PLAIN", "PSE_FP32_FP64ACC", "PSE_FP32_COMPENSATED", "PSE_THREAD_PER_TET",
+              "PSE_WARP_COOPERATIVE", "PSE_BINNED_PERSISTENT", "PSE_WARP_PER_TET"):
+        assert k in mirrored, k
+    for k in mirrored:
+        assert getattr(_lib, k) == int(defs[k]), k
+
+
+def test_compensated_accumulation_needs_overwrite(L):
+    """The compensated FP32 pairs start from a cleared output: accumulate = 1 is refused
+    before any device work."""
+    lat = _lib.Lattice()
+    lat.n[0] = lat.n[1] = lat.n[2] = 4
+    lat.box = 1.0
+    lat.periodic = 1
+    lat.particle_mass = 1.0 / 64
+    o = _lib.DepositOpts()
+    o.precision = _lib.PSE_FP32_COMPENSATED
+    o.schedule = _lib.PSE_WARP_COOPERATIVE
+    o.accumulate = 1
+    g = (ctypes.c_int64 * 3)(4, 4, 4)
+    rc = L.pse_deposit_uniform(ctypes.c_void_p(16), ctypes.byref(lat), g, ctypes.c_void_p(16), ctypes.byref(o),
+                               None, None, 0, None)
+    assert rc == _lib.PSE_ERR_UNSUPPORTED
+    assert b"compensated" in L.pse_last_error()
+
+
 def test_library_exports_every_declared_symbol(L):
     out = subprocess.run(["nm", "-D", "--defined-only", _lib.lib_path()], capture_output=True, text=True, check=True)
     exported = set(re.findall(r"\sT\s+(pse_\w+)", out.stdout))

@@ -24,6 +24,7 @@ PATHS = [
     ("fp64-thread", pse.PSE_FP64_PLAIN, pse.PSE_THREAD_PER_TET, 1e-9),
     ("fp32-thread", pse.PSE_FP32_FP64ACC, pse.PSE_THREAD_PER_TET, 1e-5),
     ("fp32-warp", pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE, 1e-5),
+    ("fp32c-warp", pse.PSE_FP32_COMPENSATED, pse.PSE_WARP_COOPERATIVE, 1e-5),
 ]
 BIN = 10 ** (6 / 64)  # ratio of one histogram bin
 

@@ -34,6 +34,8 @@ PATHS = [
     ("fp32-warp", pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE),
     ("fp32-binned", pse.PSE_FP32_FP64ACC, "binned"),
     ("fp32-warp-per-tet", pse.PSE_FP32_FP64ACC, pse.PSE_WARP_PER_TET),
+    ("fp32c-warp", pse.PSE_FP32_COMPENSATED, pse.PSE_WARP_COOPERATIVE),
+    ("fp32c-binned", pse.PSE_FP32_COMPENSATED, "binned"),
 ]
 # the binned schedule with tiny thresholds, so that small cases go through the split
 # work items (every tetrahedron with more than 4 bounding-box cells, 8 cells per item)
@@ -326,6 +328,11 @@ def test_cube_subset_and_accumulate(name, prec, sched):
     fl = density_floor(subset_tets(pos, n, a_ids), np.full(6 * len(a_ids), 1.0 / (6 * n ** 3)), g)
     e = cell_errors(out.cpu().numpy(), ref_a, floor_mass=fl)
     assert e["max_rel"] <= tol_for(prec), e
+    if prec == pse.PSE_FP32_COMPENSATED:  # the float pairs start from a cleared output
+        with pytest.raises(pse.PseError):
+            pse.deposit_uniform(dpos, n, g, precision=prec, **sched_kw(sched), cube_ids=dev(b_ids), out=out,
+                                accumulate=True)
+        return
     pse.deposit_uniform(dpos, n, g, precision=prec, **sched_kw(sched), cube_ids=dev(b_ids), out=out,
                         accumulate=True)
     e = cell_errors(out.cpu().numpy(), ref)
@@ -481,6 +488,21 @@ def test_config2_fp32_vs_fp64_gpu_all_cells():
     e = cell_errors(a, b)
     assert e["max_rel"] <= TOL32, e
     assert e["mass"] <= MASS32, e
+
+
+def test_config2_compensated_fp32_accumulation():
+    """Config 2 with compensated FP32 accumulation: the same FP32 clips as the FP64-accumulated
+    path, so the two agree far inside the clip tolerance, and both keep the oracle's mass."""
+    cfg = CONFIGS[2]
+    dpos = dev(config_positions(cfg))
+    a, sa = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, precision=pse.PSE_FP32_FP64ACC, stats=True)
+    b, sb = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, precision=pse.PSE_FP32_COMPENSATED, stats=True)
+    for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos"):
+        assert sa[k] == sb[k], k
+    e = cell_errors(b.cpu().numpy(), a.cpu().numpy())
+    assert e["max_rel"] <= 1e-9 and e["mass"] <= MASS32, e
+    raw = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, precision=pse.PSE_FP32_COMPENSATED, mass_fixup=False)
+    assert abs(float(raw.sum()) - 1.0) <= 1e-6
 
 
 def test_inverted_tetrahedra_are_counted_alike_by_every_schedule():
