@@ -43,12 +43,12 @@ L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 FLOP_PER_TET = 150.0
 FLOP_PER_BBOX_CELL = 32.0
 FLOP_PER_CLIP = 620.0
-# From one ncu capture of the tuned deposit kernel (k_warp_coop, 3 blocks of 128 threads
+# From one ncu capture of the tuned deposit kernel (k_warp_coop, 4 blocks of 128 threads
 # per SM) on the headline workload: DRAM bytes read + written per launch, and thread
 # instructions issued per partial clip (warp instructions x active lanes / partial clips).
 # Both go stale when the kernel changes and must be re-taken with it.
-DRAM_BYTES_PER_LAUNCH = 254_682_368
-THREAD_INST_PER_CLIP = 4803.4
+DRAM_BYTES_PER_LAUNCH = 301_274_624
+THREAD_INST_PER_CLIP = 5810.3
 SM_COUNT_GB300 = 152
 PRECISION = "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up"
 FP32_LANES_PER_SM = 128
@@ -301,7 +301,7 @@ def run_workload(args, cfg):
 
             def step(stats=False):
                 return pse.deposit_octree_streamed(h, n, oct_, slab, out=out, stats=stats, precision=prec,
-                                                   tuning={"blocks_per_sm": 3})
+                                                   tuning={"blocks_per_sm": 4})
             config.update({"grid": f"octree bc={cfg.bc} levels 0-{cfg.max_level} (finest {cfg.grid_n}^3)",
                            "schedule": "warp-cooperative", "streaming": f"z-slabs of {slab} cube layers from "
                                                                         "pinned host memory, double-buffered"})
@@ -346,11 +346,11 @@ def run_workload(args, cfg):
         extra["cost_model"] = {"training_s": time.perf_counter() - t0, "loss_first_last": [hist[0], hist[-1]],
                                "train_rows": int(feat.shape[0])}
         del feat, targ, feats, targs
-        arms = {"warp": dict(schedule=pse.PSE_WARP_COOPERATIVE, tuning={"blocks_per_sm": 3}, precision=prec),
+        arms = {"warp": dict(schedule=pse.PSE_WARP_COOPERATIVE, tuning={"blocks_per_sm": 4}, precision=prec),
                 "binned-bbox": dict(schedule=pse.PSE_BINNED_PERSISTENT, precision=prec,
-                                    tuning={"blocks_per_sm": 3, "split_cells": 512, "chunk_cells": 512}),
+                                    tuning={"blocks_per_sm": 4, "split_cells": 512, "chunk_cells": 512}),
                 "binned-model": dict(schedule=pse.PSE_BINNED_PERSISTENT, cost_model=model, precision=prec,
-                                     tuning={"blocks_per_sm": 3, "split_cells": 256, "chunk_cells": 512})}
+                                     tuning={"blocks_per_sm": 4, "split_cells": 256, "chunk_cells": 512})}
         arm_ms = {}
         for name, kw in arms.items():
             ms_list = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, **kw), max(1, args.steps),
@@ -402,7 +402,7 @@ def run_workload(args, cfg):
         pos_d = h.to(dev)
         i, j, k = np.meshgrid(np.arange(64), np.arange(64), np.arange(32), indexing="ij")
         ids = torch.from_numpy(np.sort((i + n * (j + n * (k + n // 2))).ravel())).to(dev)
-        pse.deposit_octree(pos_d, n, oct_, out=out, cube_ids=ids, tuning={"blocks_per_sm": 3})
+        pse.deposit_octree(pos_d, n, oct_, out=out, cube_ids=ids, tuning={"blocks_per_sm": 4})
         touched = torch.nonzero(out.view(out.shape[0], -1).abs().sum(1) > 0).ravel()  # leaves the block reaches
         fast = out[touched].cpu().numpy()
         bms = _timed(lambda: pse.deposit_octree(pos_d, n, oct_, out=out, cube_ids=ids, precision=pse.PSE_FP64_PLAIN,
@@ -640,7 +640,7 @@ def main():
             "kernel_ms": kern_ms,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": DRAM_BYTES_PER_LAUNCH if tuned == {"blocks_per_sm": 3, "schedule": "warp"}
+                         "traffic": DRAM_BYTES_PER_LAUNCH if tuned == {"blocks_per_sm": 4, "schedule": "warp"}
                          else None, "traffic_unit": "bytes per launch (ncu dram read + write)",
                          "peak_source": "measured on this GPU in this run (FP32 FMA microbenchmark, "
                                         f"{peaks['how'].split(';')[0]}); nominal {sms} SMs x {FP32_LANES_PER_SM}"

@@ -158,7 +158,7 @@ typedef struct pse_octree {
 
 typedef struct pse_tuning {
     int32_t blocks_per_sm;   /* resident 128-thread blocks per SM of the warp-cooperative kernels: 2 (up
-                                to 255 registers per thread), 3 (170) or 4 (128); <= 0: 2 */
+                                to 255 registers per thread), 3 (170) or 4 (128); <= 0: 4 */
     int32_t warps_per_block; /* reserved (8) */
     int32_t split_cells;     /* binned schedule: a tetrahedron whose bounding box has more cells than
                                 this is split across warps; <= 0: default 1024 */
@@ -392,8 +392,10 @@ PSE_API int pse_microbench_red(double *d_grid, int64_t n_cells, int64_t blocks, 
 /*
  * Bytes of device workspace an operation needs.  op = PSE_OP_*; lat may be NULL;
  * op_params: for PSE_OP_BUILD_OCTREE a host int32 max_level (required); for the deposit
- * ops a nullable host pse_deposit_opts (the binned schedule needs room for its queue).
- * Returns 0 for an unknown op.
+ * ops a nullable host pse_deposit_opts (NULL = the default warp-cooperative schedule).
+ * Every schedule but PSE_THREAD_PER_TET needs about 6 MB for the rounding residuals of
+ * guarded tetrahedra (one block per warp of the persistent grid); the binned schedule
+ * needs room for its queue on top.  Returns 0 for an unknown op.
  */
 PSE_API size_t pse_workspace_size(int op, const pse_lattice *lat, const void *op_params);
 

@@ -57,7 +57,7 @@ pse_deposit_opts default_opts()
 constexpr double kDefaultGuardEps = 1.0e-5;
 
 // resident blocks per SM of the warp-cooperative kernel (1: no register cap; 2: 128 registers)
-constexpr int kDefaultBlocksPerSm = 2;  // 128-thread blocks: 255 registers per thread
+constexpr int kDefaultBlocksPerSm = 4;  // 128-thread blocks: 128 registers per thread, 16 warps per SM
 
 float kappa_limit(double guard_eps)
 {
@@ -233,12 +233,23 @@ constexpr int kDefaultSplitCells = 1024;
 constexpr int kDefaultChunkCells = 512;
 
 // workspace of a deposit; n_tets < 0: unknown (0 is returned if it matters)
+// [Workspace header][warp kernels: residual blocks][binned: queue][cost model: bitmap]
 size_t deposit_ws_bytes(const pse_deposit_opts *o, int64_t n_tets)
 {
-    if (!o || o->schedule != PSE_BINNED_PERSISTENT) return pse::kWorkspaceBytes;
-    if (!o->cost_model) return pse::kWorkspaceBytes + pse::kQueueBytes;
+    const int sched = o ? o->schedule : PSE_WARP_COOPERATIVE;
+    if (sched == PSE_THREAD_PER_TET) return pse::kWorkspaceBytes;
+    const size_t base = pse::kWorkspaceBytes + pse::kResidualBytes;
+    if (sched != PSE_BINNED_PERSISTENT) return base;
+    if (!o->cost_model) return base + pse::kQueueBytes;
     if (n_tets < 0) return 0;
-    return pse::kWorkspaceBytes + pse::kQueueBytes + pse::qbits_bytes(n_tets);
+    return base + pse::kQueueBytes + pse::qbits_bytes(n_tets);
+}
+
+// octree deposits: the header, plus the residual blocks for the warp kernel
+size_t octree_ws_bytes(const pse_deposit_opts *o)
+{
+    return (o && o->schedule == PSE_THREAD_PER_TET) ? pse::kWorkspaceBytes
+                                                     : pse::kWorkspaceBytes + pse::kResidualBytes;
 }
 
 // h_pos != NULL: stream the lattice from host memory in z-slabs of slab_cubes cube layers
@@ -254,18 +265,22 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
     // streamed: tetrahedron ids (cost-model bitmap) are slab-local
     const int64_t n_tets = streamed ? 6 * p.nc[0] * p.nc[1] * std::min(slab_cubes, p.nc[2])
                                     : (p.src == pse::SRC_TETS) ? p.n_units : 6 * p.n_units;
-    int rc = acquire_ws(d_ws, ws_bytes, st, lease, deposit_ws_bytes(&o, n_tets), false);
+    int rc = acquire_ws(d_ws, ws_bytes, st, lease, p.leaves ? octree_ws_bytes(&o) : deposit_ws_bytes(&o, n_tets),
+                        false);
     if (rc != PSE_OK) return rc;
     p.ws = lease.ws;
+    if (o.schedule != PSE_THREAD_PER_TET)
+        p.vres = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes);
+    unsigned char *const after_res = reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes +
+                                     pse::kResidualBytes;
     size_t qbits_len = 0;
     if (binned && o.cost_model) {
         p.model = static_cast<const pse::CostModelDev *>(o.cost_model);
-        p.qbits = reinterpret_cast<uint32_t *>(reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes +
-                                               pse::kQueueBytes);
+        p.qbits = reinterpret_cast<uint32_t *>(after_res + pse::kQueueBytes);
         qbits_len = pse::qbits_bytes(n_tets);
     }
     if (binned) {
-        unsigned char *q = reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes;
+        unsigned char *q = after_res;
         p.q_tet = reinterpret_cast<int64_t *>(q);
         p.chunk_start = reinterpret_cast<int64_t *>(q + (size_t)pse::kQueueCap * 8);
         p.q_cells = reinterpret_cast<int32_t *>(q + (size_t)pse::kQueueCap * 8 + (size_t)(pse::kQueueCap + 1) * 8);
@@ -568,7 +583,7 @@ size_t pse_workspace_size(int op, const pse_lattice *lat, const void *op_params)
     case PSE_OP_DEPOSIT_TETS:
         return deposit_ws_bytes(static_cast<const pse_deposit_opts *>(op_params), -1);
     case PSE_OP_DEPOSIT_OCTREE:
-        return pse::kWorkspaceBytes;
+        return octree_ws_bytes(static_cast<const pse_deposit_opts *>(op_params));
     case PSE_OP_BUILD_OCTREE: {
         if (!op_params) return 0;
         const int32_t ml = *static_cast<const int32_t *>(op_params);

@@ -339,7 +339,8 @@ struct WarpSmem {
     int start[32];        // exclusive prefix of the pair counts
     int skip[32];         // first bounding-box cell of this record (split tetrahedra; else 0)
     int guard[32];        // 1: clip this tetrahedron in float64
-    float vlo[12][32];    // guarded tetrahedra: rounding residuals of v (exact = v + vlo)
+    float *vres;          // this warp's residual block in global memory: [12][32] floats, the
+                          // rounding residuals of guarded records (exact vertex = v + vres)
     unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
     unsigned long long gq[64]; // queued partial pairs of guarded tetrahedra (float64 clips)
     float poly[42][32];        // FP32 clip: each lane's 7 edge slots (a.xyz, b.xyz per slot)
@@ -372,7 +373,7 @@ __device__ __noinline__ double redo_fp64(const WarpSmem *S, int t, int cx, int c
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         v[q] = mk<float>(S->v[3 * q][t], S->v[3 * q + 1][t], S->v[3 * q + 2][t]);
-        r[q] = mk<float>(S->vlo[3 * q][t], S->vlo[3 * q + 1][t], S->vlo[3 * q + 2][t]);
+        r[q] = mk<float>(S->vres[(3 * q) * 32 + t], S->vres[(3 * q + 1) * 32 + t], S->vres[(3 * q + 2) * 32 + t]);
     }
     P3<double> pd[4];
     exact_vertices(v, r, cx, cy, cz, pd);
@@ -384,9 +385,9 @@ __device__ __forceinline__ void store_residuals(WarpSmem *S, int lane, const P3<
 {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        S->vlo[3 * q][lane] = r[q].x;
-        S->vlo[3 * q + 1][lane] = r[q].y;
-        S->vlo[3 * q + 2][lane] = r[q].z;
+        S->vres[(3 * q) * 32 + lane] = r[q].x;
+        S->vres[(3 * q + 1) * 32 + lane] = r[q].y;
+        S->vres[(3 * q + 2) * 32 + lane] = r[q].z;
     }
 }
 
@@ -717,6 +718,13 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
     }
 }
 
+
+// Point S->vres at this warp's residual block (every lane writes the same value).
+__device__ __forceinline__ void bind_residuals(const DepositParams &P, WarpSmem *S)
+{
+    S->vres = P.vres + ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (12 * 32);
+    __syncwarp();
+}
 
 inline int persistent_blocks(const void *kernel, int threads, size_t smem)
 {

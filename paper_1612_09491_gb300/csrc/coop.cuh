@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
+    bind_residuals(P, S);
     const int lane = threadIdx.x & 31;
     Counters cnt;
     if (STATS) cnt.zero();
@@ -215,6 +216,7 @@ cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, i
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);
+    if (blocks > kMaxWarpBlocks) blocks = kMaxWarpBlocks;
     const int64_t need = (max_items + threads / 32 - 1) / (threads / 32);
     if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
     void *args[] = {const_cast<DepositParams *>(&p)};

@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
+    bind_residuals(P, S);
     const int lane = threadIdx.x & 31;
     Counters cnt;
     if (STATS) cnt.zero();
@@ -418,7 +419,8 @@ cudaError_t launch_warp_per_tet(const DepositParams &p, bool stats, cudaStream_t
     const void *k = stats ? (const void *)k_warp_per_tet<true> : (const void *)k_warp_per_tet<false>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    const int blocks = persistent_blocks(k, threads, smem);
+    int blocks = persistent_blocks(k, threads, smem);
+    if (blocks > kMaxWarpBlocks) blocks = kMaxWarpBlocks;
     void *args[] = {const_cast<DepositParams *>(&p)};
     return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
 }

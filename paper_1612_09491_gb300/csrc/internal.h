@@ -62,6 +62,7 @@ struct DepositParams {
     double scale_d[3];         // g_a / box
     float scale_f[3];
     double *out;
+    float *vres;               // warp kernels: kMaxWarpBlocks * 4 residual blocks (see kResidualBytes)
     // numerics
     float kappa_max;           // FP32 path: tetrahedra with kappa above this clip in float64
     int32_t fixup;             // accumulate mass_target / mass_deposited for the renormalisation
@@ -87,7 +88,15 @@ struct DepositParams {
     uint32_t *qbits;           // cost model: bit t set = tetrahedron t was queued ([ceil(T/32)])
 };
 
-// binned schedule: queue capacity and the bytes it takes after the Workspace header
+// warp kernels (every schedule but thread-per-tetrahedron): the float32 rounding residuals
+// of guarded records live in global memory, one [12][32] float block per warp of the
+// grid, right after the Workspace header; their grids are capped at kMaxWarpBlocks blocks
+// of 4 warps (persistent kernels, so the cap only bounds the parallelism).  Keeping them
+// out of shared memory lets 4 blocks of 128 threads share an SM.
+constexpr int kMaxWarpBlocks = 1024;
+constexpr size_t kResidualBytes = (size_t)kMaxWarpBlocks * 4 * 12 * 32 * sizeof(float);
+
+// binned schedule: queue capacity and the bytes it takes after the residual blocks
 constexpr int64_t kQueueCap = int64_t(1) << 21;
 constexpr size_t kQueueBytes = ((size_t)kQueueCap * (8 + 4) + (size_t)(kQueueCap + 1) * 8 + 255) / 256 * 256;
 // cost-model binning: one bit per tetrahedron after the queue

@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
+    bind_residuals(P, S);
     const int lane = threadIdx.x & 31;
     Counters cnt;
     if (STATS) cnt.zero();
@@ -763,6 +764,7 @@ cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);
+    if (blocks > kMaxWarpBlocks) blocks = kMaxWarpBlocks;
     const int64_t need = (p.n_items + 3) / 4;
     if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
     void *args[] = {const_cast<DepositParams *>(&p)};

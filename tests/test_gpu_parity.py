@@ -462,7 +462,7 @@ def test_config4_full_size_sampled_cells():
     cfg = CONFIGS[4]
     pos = zeldovich_positions_device(cfg.n, cfg.spectral_index, cfg.rms_disp, cfg.seed, device="cuda")
     g = cfg.grid_n
-    m, st = pse.deposit_uniform(pos, cfg.n, g, tuning={"blocks_per_sm": 3}, stats=True)
+    m, st = pse.deposit_uniform(pos, cfg.n, g, tuning={"blocks_per_sm": 4}, stats=True)
     assert st["tets"] == cfg.n_tets
     m = m.cpu().numpy()
     assert abs(m.sum() - 1.0) <= MASS32

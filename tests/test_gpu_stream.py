@@ -156,7 +156,7 @@ def test_config5_streamed_full_size_sampled_cells():
     oct_ = pse.build_octree_streamed(h, n, bc, cfg.max_level, 64, 2.0)
     leaves = oct_.leaves()
     assert sum(8.0 ** -int(l) for l in leaves[:, 0]) == pytest.approx(1.0, abs=1e-12)
-    out, st = pse.deposit_octree_streamed(h, n, oct_, 64, stats=True, tuning={"blocks_per_sm": 3})
+    out, st = pse.deposit_octree_streamed(h, n, oct_, 64, stats=True, tuning={"blocks_per_sm": 4})
     assert st["tets"] == cfg.n_tets
     assert abs(float(out.sum()) - 1.0) <= 1e-12
     posh = h.numpy()
