@@ -343,7 +343,8 @@ struct WarpSmem {
                           // rounding residuals of guarded records (exact vertex = v + vres)
     unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
     unsigned long long gq[64]; // queued partial pairs of guarded tetrahedra (float64 clips)
-    float poly[42][32];        // FP32 clip: each lane's 7 edge slots (a.xyz, b.xyz per slot)
+    float2 poly[21][32];       // FP32 clip: each lane's 7 edge slots, 3 float2 each:
+                               // (a.x, a.y), (a.z, b.x), (b.y, b.z)
 };
 
 constexpr int kQBits = 19;  // per-axis cell offset bits in a queue entry
@@ -465,28 +466,66 @@ __device__ __forceinline__ void deposit_clip(const DepositParams &P, const WarpS
 // ---------------------------------------------------------------------------
 // The FP32 clip of the warp kernels: overlap_volume<float> (geom.cuh) with the polygon's
 // edge slots in shared memory instead of registers.  E is this lane's column of a
-// [42][32] array; slot k holds a.xyz, b.xyz in rows 6k .. 6k+5.  The arithmetic and
+// [21][32] float2 array; slot k holds a.xyz, b.xyz in rows 3k .. 3k+2.  The arithmetic and
 // its order are those of overlap_volume; only the edge loops stay rolled, so that the
-// per-edge code exists once for the two slab passes and once for the z split.  The
+// per-edge code exists once per slab pass and once for the z split.  The
 // clip dominates the deposit kernel, whose speed is set by instruction fetch as much as
 // by issue: the unrolled clip is 15 copies of the per-edge code.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void slot_store(float *E, int k, const P3<float> &a, const P3<float> &b)
+__device__ __forceinline__ void slot_store(float2 *E, int k, const P3<float> &a, const P3<float> &b)
 {
-    float *r = E + k * (6 * 32);
-    r[0] = a.x; r[32] = a.y; r[64] = a.z;
-    r[96] = b.x; r[128] = b.y; r[160] = b.z;
+    float2 *r = E + k * (3 * 32);
+    r[0] = make_float2(a.x, a.y);
+    r[32] = make_float2(a.z, b.x);
+    r[64] = make_float2(b.y, b.z);
 }
 
-__device__ __forceinline__ void slot_load(const float *E, int k, P3<float> &a, P3<float> &b)
+__device__ __forceinline__ void slot_load(const float2 *E, int k, P3<float> &a, P3<float> &b)
 {
-    const float *r = E + k * (6 * 32);
-    a = mk<float>(r[0], r[32], r[64]);
-    b = mk<float>(r[96], r[128], r[160]);
+    const float2 *r = E + k * (3 * 32);
+    const float2 u = r[0], v = r[32], w = r[64];
+    a = mk<float>(u.x, u.y, v.x);
+    b = mk<float>(v.y, w.x, w.y);
+}
+
+// One slab pass of the rolled clip (clip_slab<3 + 2 AX> of geom.cuh on the slots in E):
+// clips slots [0, ne) against lo <= c_AX < hi and appends the two new edges.  The axis is
+// a template parameter, so the x and y passes each get their own loop body without
+// per-edge axis selects (one more copy of the per-edge code, fewer instructions).
+template <int AX>
+__device__ __forceinline__ void slab_pass(float2 *E, float lo, float hi, float tol)
+{
+    using T = float;
+    constexpr int ne = 3 + 2 * AX;
+    const P3<T> z0 = mk<T>(T(0), T(0), T(0));
+    P3<T> xl = z0, nl = z0, xh = z0, nh = z0;
+#pragma unroll 1
+    for (int k = 0; k < ne; ++k) {
+        P3<T> ea, eb;
+        slot_load(E, k, ea, eb);
+        const T ca = AX ? ea.y : ea.x, cb = AX ? eb.y : eb.x;
+        const bool a_lo = ca < lo - tol, b_lo = cb < lo - tol;
+        const bool a_hi = ca >= hi - tol, b_hi = cb >= hi - tol;
+        const T inv = fdiv(T(1), cb - ca);
+        const P3<T> pa = at_plane(ea, eb, (lo - ca) * inv, AX, lo);
+        const P3<T> ph = at_plane(ea, eb, (hi - ca) * inv, AX, hi);
+        const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
+        P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
+        P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
+        na = drop ? z0 : na;
+        nb = drop ? z0 : nb;
+        slot_store(E, k, na, nb);
+        xl = (!a_lo && b_lo) ? pa : xl;
+        nl = (a_lo && !b_lo) ? pa : nl;
+        xh = (!a_hi && b_hi) ? ph : xh;
+        nh = (a_hi && !b_hi) ? ph : nh;
+    }
+    slot_store(E, ne, xl, nl);
+    slot_store(E, ne + 1, xh, nh);
 }
 
 __device__ __forceinline__ float overlap_volume_rolled(const P3<float> (&p)[4], const P3<float> (&n)[4], float lx,
-                                                       float ly, float &err, float *E)
+                                                       float ly, float &err, float2 *E)
 {
     using T = float;
     const T cx = T(0.25) * ((p[0].x + p[1].x) + (p[2].x + p[3].x));
@@ -526,35 +565,8 @@ __device__ __forceinline__ float overlap_volume_rolled(const P3<float> (&p)[4], 
         slot_store(E, 1, b, c);
         slot_store(E, 2, c, a);
         // the x and y slab passes (clip_slab<3> then clip_slab<5>)
-#pragma unroll 1
-        for (int ax = 0; ax < 2; ++ax) {
-            const int ne = 3 + 2 * ax;
-            const T lo = ax ? ylo : xlo, hi = ax ? yhi : xhi;
-            P3<T> xl = z0, nl = z0, xh = z0, nh = z0;
-#pragma unroll 1
-            for (int k = 0; k < ne; ++k) {
-                P3<T> ea, eb;
-                slot_load(E, k, ea, eb);
-                const T ca = ax ? ea.y : ea.x, cb = ax ? eb.y : eb.x;
-                const bool a_lo = ca < lo - tol, b_lo = cb < lo - tol;
-                const bool a_hi = ca >= hi - tol, b_hi = cb >= hi - tol;
-                const T inv = fdiv(T(1), cb - ca);
-                const P3<T> pa = at_plane(ea, eb, (lo - ca) * inv, ax, lo);
-                const P3<T> ph = at_plane(ea, eb, (hi - ca) * inv, ax, hi);
-                const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
-                P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
-                P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
-                na = drop ? z0 : na;
-                nb = drop ? z0 : nb;
-                slot_store(E, k, na, nb);
-                xl = (!a_lo && b_lo) ? pa : xl;
-                nl = (a_lo && !b_lo) ? pa : nl;
-                xh = (!a_hi && b_hi) ? ph : xh;
-                nh = (a_hi && !b_hi) ? ph : nh;
-            }
-            slot_store(E, ne, xl, nl);
-            slot_store(E, ne + 1, xh, nh);
-        }
+        slab_pass<0>(E, xlo, xhi, tol);
+        slab_pass<1>(E, ylo, yhi, tol);
         // the z split with the three integrals (split_zslab<7>)
         {
             P3<T> xl = z0, nl = z0, xh = z0, nh = z0;
