@@ -145,6 +145,14 @@ def test_workspace_size(L):
     binned = pse.workspace_size(_lib.PSE_OP_DEPOSIT_UNIFORM, schedule=_lib.PSE_BINNED_PERSISTENT)
     assert plain == L.pse_workspace_size(_lib.PSE_OP_DEPOSIT_UNIFORM, None, None)
     assert binned > plain + (1 << 20)
+    # the thread-per-tetrahedron kernels need the header only; the warp kernels add one
+    # [12][32]-float residual block per warp of their (capped) persistent grid
+    thread = pse.workspace_size(_lib.PSE_OP_DEPOSIT_UNIFORM, schedule=_lib.PSE_THREAD_PER_TET)
+    assert 64 <= thread < 4096
+    assert plain >= thread + 1024 * 4 * 12 * 32 * 4
+    oct_warp = pse.workspace_size(_lib.PSE_OP_DEPOSIT_OCTREE)
+    oct_thread = pse.workspace_size(_lib.PSE_OP_DEPOSIT_OCTREE, schedule=_lib.PSE_THREAD_PER_TET)
+    assert oct_thread == thread and oct_warp == plain
 
 
 def test_octree_leaf_validation_needs_no_gpu(L):

@@ -490,6 +490,22 @@ def test_config2_fp32_vs_fp64_gpu_all_cells():
     assert e["mass"] <= MASS32, e
 
 
+def test_compensated_graph_replay_and_binned_split():
+    """Compensated accumulation through a captured graph (the pair conversion is part of the
+    replayed sequence) and through the binned schedule's split work items."""
+    n, g = 16, 32
+    pos = zeldovich_positions(n, -2.0, 1.5, seed=23)
+    ref, _ = oracle.deposit_lattice(pos, n, g)
+    dpos = dev(pos)
+    ws = torch.empty(pse.workspace_size(schedule=pse.PSE_BINNED_PERSISTENT), dtype=torch.uint8, device="cuda")
+    out = torch.empty((g, g, g), dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        pse.deposit_uniform(dpos, n, g, out=out, workspace=ws, precision=pse.PSE_FP32_COMPENSATED,
+                            schedule=pse.PSE_BINNED_PERSISTENT, tuning=dict(SPLIT_TUNING, use_graph=1))
+        e = cell_errors(out.cpu().numpy(), ref)
+        assert e["max_rel"] <= TOL32 and e["mass"] <= MASS32, e
+
+
 def test_config2_compensated_fp32_accumulation():
     """Config 2 with compensated FP32 accumulation: the same FP32 clips as the FP64-accumulated
     path, so the two agree far inside the clip tolerance, and both keep the oracle's mass."""

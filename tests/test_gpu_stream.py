@@ -46,6 +46,19 @@ def test_uniform_streamed_equals_one_shot(slab, sched):
     assert e["max_rel"] <= 2e-6 and e["mass"] <= 1e-13, e
 
 
+def test_uniform_streamed_compensated_equals_one_shot():
+    """Compensated accumulation across slabs: the float pairs persist over every slab and are
+    converted once at the end."""
+    cfg = CONFIGS[1]
+    pos = config_positions(cfg)
+    ref = pse.deposit_uniform(torch.from_numpy(pos).cuda(), cfg.n, cfg.grid_n,
+                              precision=pse.PSE_FP32_COMPENSATED).cpu().numpy()
+    got = pse.deposit_uniform_streamed(torch.from_numpy(pos).pin_memory(), cfg.n, cfg.grid_n, 5,
+                                       precision=pse.PSE_FP32_COMPENSATED).cpu().numpy()
+    e = cell_errors(got, ref)
+    assert e["max_rel"] <= 2e-6 and e["mass"] <= 1e-13, e
+
+
 def test_uniform_streamed_fp64_matches_oracle_from_pageable_memory():
     n, g = 12, 20
     pos = zeldovich_positions(n, -2.0, 1.5, seed=31)
