@@ -463,148 +463,6 @@ __device__ __forceinline__ void deposit_clip(const DepositParams &P, const WarpS
     }
 }
 
-// ---------------------------------------------------------------------------
-// The FP32 clip of the warp kernels: overlap_volume<float> (geom.cuh) with the polygon's
-// edge slots in shared memory instead of registers.  E is this lane's column of a
-// [21][32] float2 array; slot k holds a.xyz, b.xyz in rows 3k .. 3k+2.  The arithmetic and
-// its order are those of overlap_volume; only the edge loops stay rolled, so that the
-// per-edge code exists once per slab pass and once for the z split.  The
-// clip dominates the deposit kernel, whose speed is set by instruction fetch as much as
-// by issue: the unrolled clip is 15 copies of the per-edge code.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void slot_store(float2 *E, int k, const P3<float> &a, const P3<float> &b)
-{
-    float2 *r = E + k * (3 * 32);
-    r[0] = make_float2(a.x, a.y);
-    r[32] = make_float2(a.z, b.x);
-    r[64] = make_float2(b.y, b.z);
-}
-
-__device__ __forceinline__ void slot_load(const float2 *E, int k, P3<float> &a, P3<float> &b)
-{
-    const float2 *r = E + k * (3 * 32);
-    const float2 u = r[0], v = r[32], w = r[64];
-    a = mk<float>(u.x, u.y, v.x);
-    b = mk<float>(v.y, w.x, w.y);
-}
-
-// One slab pass of the rolled clip (clip_slab<3 + 2 AX> of geom.cuh on the slots in E):
-// clips slots [0, ne) against lo <= c_AX < hi and appends the two new edges.  The axis is
-// a template parameter, so the x and y passes each get their own loop body without
-// per-edge axis selects (one more copy of the per-edge code, fewer instructions).
-template <int AX>
-__device__ __forceinline__ void slab_pass(float2 *E, float lo, float hi, float tol)
-{
-    using T = float;
-    constexpr int ne = 3 + 2 * AX;
-    const P3<T> z0 = mk<T>(T(0), T(0), T(0));
-    P3<T> xl = z0, nl = z0, xh = z0, nh = z0;
-#pragma unroll 1
-    for (int k = 0; k < ne; ++k) {
-        P3<T> ea, eb;
-        slot_load(E, k, ea, eb);
-        const T ca = AX ? ea.y : ea.x, cb = AX ? eb.y : eb.x;
-        const bool a_lo = ca < lo - tol, b_lo = cb < lo - tol;
-        const bool a_hi = ca >= hi - tol, b_hi = cb >= hi - tol;
-        const T inv = fdiv(T(1), cb - ca);
-        const P3<T> pa = at_plane(ea, eb, (lo - ca) * inv, AX, lo);
-        const P3<T> ph = at_plane(ea, eb, (hi - ca) * inv, AX, hi);
-        const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
-        P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
-        P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
-        na = drop ? z0 : na;
-        nb = drop ? z0 : nb;
-        slot_store(E, k, na, nb);
-        xl = (!a_lo && b_lo) ? pa : xl;
-        nl = (a_lo && !b_lo) ? pa : nl;
-        xh = (!a_hi && b_hi) ? ph : xh;
-        nh = (a_hi && !b_hi) ? ph : nh;
-    }
-    slot_store(E, ne, xl, nl);
-    slot_store(E, ne + 1, xh, nh);
-}
-
-__device__ __forceinline__ float overlap_volume_rolled(const P3<float> (&p)[4], const P3<float> (&n)[4], float lx,
-                                                       float ly, float &err, float2 *E)
-{
-    using T = float;
-    const T cx = T(0.25) * ((p[0].x + p[1].x) + (p[2].x + p[3].x));
-    const T cy = T(0.25) * ((p[0].y + p[1].y) + (p[2].y + p[3].y));
-    const T cz = T(0.25) * ((p[0].z + p[1].z) + (p[2].z + p[3].z));
-    const P3<T> q = mk<T>(floor(fmin(fmax(cx, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256),
-                          floor(fmin(fmax(cy, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256),
-                          floor(fmin(fmax(cz, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256));
-    P3<T> pl[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) pl[i] = sub(p[i], q);
-    const T xlo = -q.x, xhi = T(1) - q.x, ylo = -q.y, yhi = T(1) - q.y, zlo = -q.z, zhi = T(1) - q.z;
-    const T xc = T(0.5) - q.x, yc = T(0.5) - q.y;
-    const T lc = fmin(fmax((cz - q.z) + lx * (xc - (cx - q.x)) + ly * (yc - (cy - q.y)), zlo), zhi);
-    const T l0 = lc - lx * xc - ly * yc;
-    const P3<T> z0 = mk<T>(T(0), T(0), T(0));
-
-    T vol = T(0), mag = T(0);
-#pragma unroll 1
-    for (int f = 0; f < 4; ++f) {
-        int ia, ib, ic;
-        face_vertices(f, ia, ib, ic);
-        const P3<T> a = pick4(pl, ia), b = pick4(pl, ib), c = pick4(pl, ic);
-        const T mnx = fmin(a.x, fmin(b.x, c.x)), mxx = fmax(a.x, fmax(b.x, c.x));
-        const T mny = fmin(a.y, fmin(b.y, c.y)), mxy = fmax(a.y, fmax(b.y, c.y));
-        if (mxx < xlo || mnx >= xhi || mxy < ylo || mny >= yhi) continue;
-        const P3<T> nf = (f == 0) ? n[0] : (f == 1) ? n[1] : (f == 2) ? n[2] : n[3];
-        if (nf.z == T(0)) continue;
-        const T mnz = fmin(a.z, fmin(b.z, c.z)), mxz = fmax(a.z, fmax(b.z, c.z));
-        const T cmag = fmax(T(1), fmax(fmax(fmax(fabs(mnx), fabs(mxx)), fmax(fabs(mny), fabs(mxy))),
-                                       fmax(fabs(mnz), fabs(mxz))));
-        const T tol = T(8) * roundoff<T>() * cmag;
-        const T sc = fdiv(dot(nf, a), dot(nf, nf));
-        const P3<T> o = mk<T>(sc * nf.x, sc * nf.y, sc * nf.z);
-
-        slot_store(E, 0, a, b);
-        slot_store(E, 1, b, c);
-        slot_store(E, 2, c, a);
-        // the x and y slab passes (clip_slab<3> then clip_slab<5>)
-        slab_pass<0>(E, xlo, xhi, tol);
-        slab_pass<1>(E, ylo, yhi, tol);
-        // the z split with the three integrals (split_zslab<7>)
-        {
-            P3<T> xl = z0, nl = z0, xh = z0, nh = z0;
-            T below = T(0), above = T(0), mid = T(0);
-            const T fo = o.z - fmaT(lx, o.x, fmaT(ly, o.y, l0));
-#pragma unroll 1
-            for (int k = 0; k < 7; ++k) {
-                P3<T> ea, eb;
-                slot_load(E, k, ea, eb);
-                const bool a_lo = ea.z < zlo - tol, b_lo = eb.z < zlo - tol;
-                const bool a_hi = ea.z >= zhi - tol, b_hi = eb.z >= zhi - tol;
-                const T inv = fdiv(T(1), eb.z - ea.z);
-                const P3<T> pa = at_plane(ea, eb, (zlo - ea.z) * inv, 2, zlo);
-                const P3<T> ph = at_plane(ea, eb, (zhi - ea.z) * inv, 2, zhi);
-                const P3<T> ba = a_lo ? ea : pa, bb = b_lo ? eb : pa;
-                below += (a_lo || b_lo) ? fan_const(ba, bb, zlo, l0, lx, ly) : T(0);
-                const P3<T> ua = a_hi ? ea : ph, ub = b_hi ? eb : ph;
-                above += (a_hi || b_hi) ? fan_const(ua, ub, zhi, l0, lx, ly) : T(0);
-                const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
-                const P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
-                const P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
-                mid += drop ? T(0) : fan_mid(na, nb, o, fo, l0, lx, ly);
-                xl = (!a_lo && b_lo) ? pa : xl;
-                nl = (a_lo && !b_lo) ? pa : nl;
-                xh = (!a_hi && b_hi) ? ph : xh;
-                nh = (a_hi && !b_hi) ? ph : nh;
-            }
-            below += fan_const(nl, xl, zlo, l0, lx, ly);
-            above += fan_const(nh, xh, zhi, l0, lx, ly);
-            mid += fan_mid(xl, nl, o, fo, l0, lx, ly) + fan_mid(xh, nh, o, fo, l0, lx, ly);
-            mag += fabs(below) + fabs(above) + fabs(mid);
-            vol += below + above + mid;
-        }
-    }
-    err = mag * T(1.0 / 6.0);
-    return vol * T(1.0 / 6.0);
-}
-
 // FP32 clips of the first `count` entries of S->q (tetrahedra below the guard).
 template <bool STATS, bool OCT, Acc A>
 __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
