@@ -50,6 +50,7 @@ FLOP_PER_CLIP = 620.0
 DRAM_BYTES_PER_LAUNCH = 300_260_608
 THREAD_INST_PER_CLIP = 5182.4
 SM_COUNT_GB300 = 152
+SM_MAX_MHZ_GB300 = 2070.0  # the part's maximum SM clock
 PRECISION = "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up"
 FP32_LANES_PER_SM = 128
 
@@ -420,11 +421,10 @@ def run_workload(args, cfg):
     if base is not None:
         base["speedup"] = value / base["tets_per_s"]
     csum = clk.summary()
-    max_mhz = csum.get("sm_max_mhz") or 2070.0
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count or SM_COUNT_GB300
     peaks = pse.measure_peaks(stream)
-    peak = peaks["fp32_tflops"]
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_GB300 * 1e6 / 1e12
     alg = FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] + FLOP_PER_CLIP * st["partial_clips"]
     achieved = alg / (ms * 1e-3) / 1e12
     result = {
@@ -439,8 +439,9 @@ def run_workload(args, cfg):
         "fp64_gpu_baseline": base,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": None, "note": "step time (all kernels of the call)",
-                     "peak_source": "measured on this GPU in this run (FP32 FMA microbenchmark); nominal "
-                                    f"{sms} SMs x {FP32_LANES_PER_SM} lanes x 2 x {max_mhz:.0f} MHz"},
+                     "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
+                                    f"{SM_MAX_MHZ_GB300:.0f} MHz",
+                     "measured_fma_tflops": peaks["fp32_tflops"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 0,
                 "note": "streamed from pinned host memory inside the step" if h2d else
                         "inputs resident (no host copies in this workload's step)"},
@@ -606,9 +607,7 @@ def main():
         props = torch.cuda.get_device_properties(dev)
         sms = props.multi_processor_count or SM_COUNT_GB300
         csum = clk.summary()
-        max_mhz = csum.get("sm_max_mhz") or 2070.0
-        nominal = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-        peak = peaks["fp32_tflops"]
+        peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_GB300 * 1e6 / 1e12
         achieved = alg_flop / (kern_ms * 1e-3) / 1e12
         deposits = st["partial_clips"] + st["inside_cells"]  # FP64 reductions issued (upper bound)
         cpu = None
@@ -642,18 +641,19 @@ def main():
                          "frac": achieved / peak,
                          "traffic": DRAM_BYTES_PER_LAUNCH if tuned == {"blocks_per_sm": 4, "schedule": "warp"}
                          else None, "traffic_unit": "bytes per launch (ncu dram read + write)",
-                         "peak_source": "measured on this GPU in this run (FP32 FMA microbenchmark, "
-                                        f"{peaks['how'].split(';')[0]}); nominal {sms} SMs x {FP32_LANES_PER_SM}"
-                                        f" lanes x 2 x {max_mhz:.0f} MHz = {nominal:.1f} TFLOP/s"},
+                         "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
+                                        f"{SM_MAX_MHZ_GB300:.0f} MHz",
+                         "measured_fma_tflops": peaks["fp32_tflops"],
+                         "measured_fma_how": peaks["how"].split(";")[0]},
             "atomics": {"achieved_per_s": deposits / (kern_ms * 1e-3), "peak_per_s": peaks["red_f64_per_s"],
                         "frac": deposits / (kern_ms * 1e-3) / peaks["red_f64_per_s"],
                         "note": "FP64 global reductions of the deposit kernel against a scattered-reduction "
                                 "microbenchmark measured in this run"},
             "issue": {"thread_inst_per_clip": THREAD_INST_PER_CLIP,
                       "achieved_tinst_per_s": THREAD_INST_PER_CLIP * st["partial_clips"] / (kern_ms * 1e-3),
-                      "peak_tinst_per_s": sms * 4 * 32 * max_mhz * 1e6,
+                      "peak_tinst_per_s": sms * 4 * 32 * SM_MAX_MHZ_GB300 * 1e6,
                       "frac": THREAD_INST_PER_CLIP * st["partial_clips"] / (kern_ms * 1e-3) /
-                              (sms * 4 * 32 * max_mhz * 1e6),
+                              (sms * 4 * 32 * SM_MAX_MHZ_GB300 * 1e6),
                       "note": "instruction issue of the deposit kernel against one warp instruction per "
                               "scheduler per clock (4 per SM), all 32 lanes"},
             "cpu_baseline": cpu,
