@@ -242,7 +242,8 @@ PSE_API int pse_build_octree_from_tet_sizes(const float *d_pos, const pse_lattic
  * Deposit the tessellation (or opts->d_cube_ids) onto the leaf blocks of `oct`:
  * d_leaf_mass[l * bc^3 + cx + bc (cy + bc cz)] (+)= sum_t m_t/|V_t| vol(T_t ∩ C) for cell
  * (cx, cy, cz) of leaf l.  Periodic lattices only.  Other arguments as
- * pse_deposit_uniform (d_leaf_mass has oct->n_cells float64 entries).
+ * pse_deposit_uniform (d_leaf_mass has oct->n_cells float64 entries), except the
+ * workspace: ws_bytes >= pse_workspace_size(PSE_OP_DEPOSIT_OCTREE, lat, opts).
  */
 PSE_API int pse_deposit_octree(const float *d_pos, const pse_lattice *lat, const pse_octree *oct,
                                double *d_leaf_mass, const pse_deposit_opts *opts, pse_deposit_stats *h_stats,
