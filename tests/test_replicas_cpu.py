@@ -54,3 +54,22 @@ def test_single_replica():
     import bench
     ms, value = bench.replica_throughput([2.0, 4.0], 600)
     assert ms == 3.0 and value == pytest.approx(2e5)
+
+
+def test_clock_summary_reads_throttle_reasons():
+    """The bench's clock record: median SM clock under load, the maximum clock, and every
+    throttle reason seen Active in any sample (nvidia-smi csv rows, faked here)."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    cs = bench.ClockSampler(None)
+    assert cs.summary()["reasons"] == ["unavailable"]
+    rows = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
+    cs.rows = [[p.strip() for p in r.split(",")] for r in rows]
+    s = cs.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    cs.rows.append([p.strip() for p in "0, 1500, 2070, 700, 0x40, Not Active, Active, Not Active, Not Active".split(",")])
+    assert cs.summary()["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
