@@ -506,6 +506,26 @@ def test_compensated_graph_replay_and_binned_split():
         assert e["max_rel"] <= TOL32 and e["mass"] <= MASS32, e
 
 
+@pytest.mark.parametrize("sched", [pse.PSE_THREAD_PER_TET, pse.PSE_WARP_PER_TET])
+def test_compensated_accumulation_in_the_baseline_kernels(sched):
+    """The thread-per-tetrahedron and warp-per-tetrahedron kernels take the accumulation mode
+    at run time; with compensated pairs they match the oracle like the tuned kernels, on a
+    uniform grid and (thread per tetrahedron) on an adaptive octree."""
+    n, g = 16, 32
+    pos = zeldovich_positions(n, -2.0, 1.5, seed=24)
+    ref, _ = oracle.deposit_lattice(pos, n, g)
+    got = pse.deposit_uniform(dev(pos), n, g, precision=pse.PSE_FP32_COMPENSATED, schedule=sched).cpu().numpy()
+    e = cell_errors(got, ref)
+    assert e["max_rel"] <= TOL32 and e["mass"] <= MASS32, e
+    if sched == pse.PSE_THREAD_PER_TET:
+        dpos = dev(pos)
+        oct_ = pse.build_octree_from_tet_sizes(dpos, n, 4, 3, 2.0)
+        o, _ = oracle.deposit_octree(pos, n, oct_.leaves(), 4, 3)
+        m = pse.deposit_octree(dpos, n, oct_, precision=pse.PSE_FP32_COMPENSATED, schedule=sched).cpu().numpy()
+        e = cell_errors(m, o)
+        assert e["max_rel"] <= TOL32 and e["mass"] <= MASS32, e
+
+
 def test_config2_compensated_fp32_accumulation():
     """Config 2 with compensated FP32 accumulation: the same FP32 clips as the FP64-accumulated
     path, so the two agree far inside the clip tolerance, and both keep the oracle's mass."""
