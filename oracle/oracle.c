@@ -705,7 +705,9 @@ static int make_fine_map(octree_t *T)
     return OR_OK;
 }
 
-static void deposit_one_tet_octree(const double p[4][3], double m_t, const octree_t *T, double *mass, ostats_t *st)
+/* Returns OR_OK, or OR_ERR_MEM if the list of touched (leaf, periodic image) pairs
+ * could not grow (nothing is deposited for this tetrahedron then). */
+static int deposit_one_tet_octree(const double p[4][3], double m_t, const octree_t *T, double *mass, ostats_t *st)
 {
     const double box = T->box;
     const int64_t F = T->fine;
@@ -723,7 +725,7 @@ static void deposit_one_tet_octree(const double p[4][3], double m_t, const octre
             k[a] = (fu - f[a]) / F;
         }
         st->degenerate_tets += 1;
-        if (!T->periodic && (k[0] || k[1] || k[2])) { st->lost_mass += m_t; return; }
+        if (!T->periodic && (k[0] || k[1] || k[2])) { st->lost_mass += m_t; return OR_OK; }
         int32_t leaf = T->fine_map[f[0] + F * (f[1] + F * f[2])];
         const int32_t *L = T->leaves + 4 * leaf;
         double side = box / (double)(1LL << L[0]), h = side / bc;
@@ -735,7 +737,7 @@ static void deposit_one_tet_octree(const double p[4][3], double m_t, const octre
             if (cc[a] >= bc) cc[a] = bc - 1;
         }
         mass[leaf * bc3 + cc[0] + bc * (cc[1] + bc * cc[2])] += m_t;
-        return;
+        return OR_OK;
     }
     double rho = m_t / vol;
     double mn[3], mx[3];
@@ -746,9 +748,10 @@ static void deposit_one_tet_octree(const double p[4][3], double m_t, const octre
         f0[a] = (int64_t)floor(mn[a] / df);
         f1[a] = (int64_t)floor(mx[a] / df);
     }
-    /* distinct (leaf, periodic image) pairs touched by the bounding box */
-    int64_t keys[512][4];
-    int nk = 0;
+    /* distinct (leaf, periodic image) pairs touched by the bounding box; the list grows
+     * on the heap, so a large tetrahedron over a deep tree keeps every leaf it touches */
+    int64_t (*keys)[4] = NULL;
+    int64_t nk = 0, cap = 0;
     for (int64_t fz = f0[2]; fz <= f1[2]; ++fz)
         for (int64_t fy = f0[1]; fy <= f1[1]; ++fy)
             for (int64_t fx = f0[0]; fx <= f1[0]; ++fx) {
@@ -757,15 +760,21 @@ static void deposit_one_tet_octree(const double p[4][3], double m_t, const octre
                 if (!T->periodic && (k[0] || k[1] || k[2])) continue;
                 int64_t leaf = T->fine_map[g[0] + F * (g[1] + F * g[2])];
                 int dup = 0;
-                for (int q = 0; q < nk && !dup; ++q)
+                for (int64_t q = 0; q < nk && !dup; ++q)
                     dup = keys[q][0] == leaf && keys[q][1] == k[0] && keys[q][2] == k[1] && keys[q][3] == k[2];
-                if (!dup && nk < 512) {
-                    keys[nk][0] = leaf; keys[nk][1] = k[0]; keys[nk][2] = k[1]; keys[nk][3] = k[2];
-                    ++nk;
+                if (dup) continue;
+                if (nk == cap) {
+                    int64_t ncap = cap ? 2 * cap : 64;
+                    int64_t (*grown)[4] = (int64_t (*)[4])realloc(keys, (size_t)ncap * sizeof(*keys));
+                    if (!grown) { free(keys); return OR_ERR_MEM; }
+                    keys = grown;
+                    cap = ncap;
                 }
+                keys[nk][0] = leaf; keys[nk][1] = k[0]; keys[nk][2] = k[1]; keys[nk][3] = k[2];
+                ++nk;
             }
     double deposited = 0.0;
-    for (int q = 0; q < nk; ++q) {
+    for (int64_t q = 0; q < nk; ++q) {
         const int32_t *L = T->leaves + 4 * keys[q][0];
         double side = box / (double)(1LL << L[0]), h = side / bc;
         double lo[3];
@@ -801,7 +810,9 @@ static void deposit_one_tet_octree(const double p[4][3], double m_t, const octre
                     }
                 }
     }
+    free(keys);
     if (!T->periodic) st->lost_mass += m_t - deposited;
+    return OR_OK;
 }
 
 /* leaf_mass [n_leaves * bc^3]: block of leaf l at l*bc^3, cells x fastest */
@@ -831,6 +842,7 @@ int oracle_deposit_octree(const float *pos, const int64_t n[3], double box, int 
         }
     }
     double m_t = particle_mass / 6.0;
+    int failed = 0;
 #pragma omp parallel for num_threads(nt) schedule(static)
     for (int64_t q = 0; q < ncube; ++q) {
         int tid = 0;
@@ -843,8 +855,16 @@ int oracle_deposit_octree(const float *pos, const int64_t n[3], double box, int 
         for (int s = 0; s < 6; ++s) {
             double p[4][3];
             lattice_tet(pos, n, box, periodic, i, j, k, s, p);
-            deposit_one_tet_octree(p, m_t, &T, priv[tid], &pst[tid]);
+            if (deposit_one_tet_octree(p, m_t, &T, priv[tid], &pst[tid]) != OR_OK) {
+#pragma omp atomic write
+                failed = 1;
+            }
         }
+    }
+    if (failed) {
+        for (int t = 0; t < nt; ++t) free(priv[t]);
+        free(priv); free(pst); free(T.fine_map);
+        return OR_ERR_MEM;
     }
     memset(leaf_mass, 0, (size_t)ncell * sizeof(double));
     ostats_t tot = {0, 0, 0, 0, 0, 0};

@@ -134,3 +134,19 @@ def test_count_rule_undisplaced_lattice_closed_form(thr):
         lev += 1
     assert set(leaves[:, 0].tolist()) == {lev}
     assert len(leaves) == 8 ** lev
+
+
+def test_large_tetrahedra_over_deep_tree_keep_every_leaf():
+    """Eq. 1 on an octree: a tetrahedron covers every leaf its volume reaches, however many.
+    A 3^3 lattice has tetrahedra a third of the box wide; on a tree refined to level 5 each
+    one's bounding box spans about 11^3 finest nodes (over a thousand leaves).  Summed onto
+    the finest uniform grid the leaves must give the uniform deposit, and the total mass 1."""
+    n, bc, lev = 3, 2, 5
+    pos = zeldovich_positions(n, -2.0, 0.3, seed=21)
+    side = 2 ** lev
+    leaves = np.array([[lev, x, y, z] for z in range(side) for y in range(side) for x in range(side)], np.int32)
+    m, _ = oracle.deposit_octree(pos, n, leaves, bc, lev, nthreads=4)
+    assert abs(m.sum() - 1.0) < 1e-12
+    g = bc * side
+    u, _ = oracle.deposit_lattice(pos, n, g, nthreads=4)
+    np.testing.assert_allclose(coarsen_to_uniform(m, leaves, bc, g), u, rtol=1e-11, atol=1e-18)
