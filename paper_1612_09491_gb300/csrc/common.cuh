@@ -337,8 +337,10 @@ struct WarpSmem {
     int org[3][32];       // octree: the leaf's first cell, base-cell frame
     float rho[32];        // 6 m_t / |6V| (deposit = rho * overlap volume, formed in float32)
     int start[32];        // exclusive prefix of the pair counts
-    int skip[32];         // first bounding-box cell of this record (split tetrahedra; else 0)
+    int skip[32];         // first pair of this record (split tetrahedra; else 0)
     int guard[32];        // 1: clip this tetrahedron in float64
+    int cut[32];          // octree: 1 if the record's cell range starts above the tetrahedron's
+                          // own first layer along its divergence axis (a leaf block cuts it)
     float *vres;          // this warp's residual block in global memory: [12][32] floats, the
                           // rounding residuals of guarded records (exact vertex = v + vres)
     unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
@@ -422,7 +424,92 @@ __device__ __forceinline__ void store_record(WarpSmem *S, int lane, const TetSet
     S->axis[lane] = ts.axis;
     S->guard[lane] = guard;
     S->skip[lane] = skip;
+    S->cut[lane] = 0;
     if (guard) store_residuals(S, lane, res);
+}
+
+// ---------------------------------------------------------------------------
+// Column runs.  A tetrahedron below the FP32 guard is enumerated by runs of up to kRun
+// cells along its divergence axis C (to_axis: A = C + 1, B = C + 2 mod 3): pair index
+// ia + dA (ib + dB w) is the run of cells (A, B) = (lo_A + ia, lo_B + ib) and C in
+// [lo_C + kRun w, lo_C + kRun w + kw).  One column clip (column_volumes) serves the run.
+// ---------------------------------------------------------------------------
+constexpr int kRun = 2;  // longer runs lose accuracy: the level terms grow with the run's height
+
+__device__ __forceinline__ int axis_a(int C) { return C == 2 ? 0 : C + 1; }
+__device__ __forceinline__ int axis_b(int C) { return C == 0 ? 2 : C - 1; }
+
+// pairs of an unguarded record: its runs
+__device__ __forceinline__ int64_t run_count(const int (&dim)[3], int C)
+{
+    const int dC = C == 0 ? dim[0] : (C == 1 ? dim[1] : dim[2]);
+    const int dA = C == 2 ? dim[0] : (C == 0 ? dim[1] : dim[2]);
+    const int dB = C == 0 ? dim[2] : (C == 1 ? dim[0] : dim[1]);
+    return (int64_t)dA * dB * ((dC + kRun - 1) / kRun);
+}
+
+// Run (ia, ib, w) of record t: base-frame first cell (cx, cy, cz) and length kw.
+__device__ __forceinline__ void run_cells(const WarpSmem *S, int t, int ia, int ib, int w, int &cx, int &cy, int &cz,
+                                          int &kw)
+{
+    const int C = S->axis[t], A = axis_a(C), B = axis_b(C);
+    kw = min(kRun, S->dim[C][t] - w * kRun);
+    const int la = S->lo[A][t] + ia, lb = S->lo[B][t] + ib, lc = S->lo[C][t] + w * kRun;
+    cx = C == 0 ? lc : (C == 1 ? lb : la);
+    cy = C == 1 ? lc : (C == 2 ? lb : la);
+    cz = C == 2 ? lc : (C == 0 ? lb : la);
+}
+
+// Run number `local` of record t (ia fastest, then ib, then w).
+__device__ __forceinline__ void run_of(const WarpSmem *S, int t, int local, int &ia, int &ib, int &w, int &cx,
+                                       int &cy, int &cz, int &kw)
+{
+    const int C = S->axis[t];
+    const int dA = S->dim[axis_a(C)][t], dB = S->dim[axis_b(C)][t];
+    ia = local % dA;
+    const int r = local / dA;
+    ib = r % dB;
+    w = r / dB;
+    run_cells(S, t, ia, ib, w, cx, cy, cz, kw);
+}
+
+// A record's cell offsets must fit the kQBits-bit fields of a queue entry.
+__device__ __forceinline__ bool dims_fit_queue(const int (&dim)[3])
+{
+    return dim[0] < (1 << 19) && dim[1] < (1 << 19) && dim[2] < (1 << 19);
+}
+
+// Record t as column_volumes reads it: vertices relative to the run's first cell (fx, fy,
+// fz) and normals, relabelled so that the divergence axis C is z, read from shared memory.
+struct RecordRun {
+    const WarpSmem *S;
+    int t, C;
+    float fx, fy, fz;
+    __device__ __forceinline__ P3<float> vtx(int i) const
+    {
+        return to_axis(mk<float>(S->v[3 * i][t] - fx, S->v[3 * i + 1][t] - fy, S->v[3 * i + 2][t] - fz), C);
+    }
+    __device__ __forceinline__ P3<float> nrm(int f) const
+    {
+        return to_axis(mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]), C);
+    }
+};
+
+// Classify the box of kw cells from cell (cx, cy, cz) along axis C against record t's
+// face planes (classify_cell for kw = 1).
+__device__ __forceinline__ int classify_run(const WarpSmem *S, int t, int C, float cx, float cy, float cz, int kw)
+{
+    bool inside = true, outside = false;
+    const float ext = (float)(kw - 1);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const float nx = S->n[3 * f][t], ny = S->n[3 * f + 1][t], nz = S->n[3 * f + 2][t];
+        const float nc = C == 0 ? nx : (C == 1 ? ny : nz);
+        const float s = fmaf(nx, cx, fmaf(ny, cy, fmaf(nz, cz, -S->e[f][t])));
+        inside = inside && (s + fmaf(ext, fmaxf(nc, 0.f), S->pos[f][t]) <= 0.f);
+        outside = outside || (s + fmaf(ext, fminf(nc, 0.f), S->neg[f][t]) >= 0.f);
+    }
+    return outside ? CELL_OUTSIDE : (inside ? CELL_INSIDE : CELL_PARTIAL);
 }
 
 // Add m to cell (cx, cy, cz) (base-cell frame) of virtual tetrahedron t: the uniform
@@ -491,6 +578,49 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
     __syncwarp();
 }
 
+// Column clips of the first `count` entries of S->q (runs of unguarded tetrahedra).
+template <bool STATS, bool OCT, Acc A>
+__device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
+{
+    if (lane < count) {
+        const unsigned long long ent = S->q[lane];
+        const int t = (int)(ent & 31u);
+        const int w = (int)((ent >> (5 + 2 * kQBits)) & kQMask);
+        const int C = S->axis[t];
+        int cx, cy, cz, kw;
+        run_cells(S, t, (int)((ent >> 5) & kQMask), (int)((ent >> (5 + kQBits)) & kQMask), w, cx, cy, cz, kw);
+        const RecordRun src{S, t, C, (float)cx, (float)cy, (float)cz};
+        float vol[kRun];
+        column_volumes<kRun>(src, S->lx[t], S->ly[t], kw, w > 0 || S->cut[t] != 0, vol, &S->poly[0][lane]);
+        const float rho = S->rho[t];
+#pragma unroll
+        for (int j = 0; j < kRun; ++j) {
+            const int ex = cx + (C == 0 ? j : 0), ey = cy + (C == 1 ? j : 0), ez = cz + (C == 2 ? j : 0);
+            if (STATS && j < kw) {
+                // the same per-cell classification as the cell schedules, for the counters
+                P3<float> n[4];
+                float e[4], ps[4], ng[4];
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
+                    e[f] = S->e[f][t];
+                    ps[f] = S->pos[f][t];
+                    ng[f] = S->neg[f][t];
+                }
+                const int cls = classify_cell<float>(n, e, ps, ng, (float)ex, (float)ey, (float)ez);
+                if (cls == CELL_PARTIAL) cnt.u[ST_PARTIAL_CLIPS]++;
+                else if (cls == CELL_INSIDE) cnt.u[ST_INSIDE_CELLS]++;
+            }
+            if (j < kw && vol[j] > 0.f) {
+                const double m = (double)(rho * vol[j]);
+                cnt.dep += m;
+                if (!deposit_pair<OCT, A>(P, S, t, ex, ey, ez, m) && STATS) cnt.dropped += m;
+            }
+        }
+    }
+    __syncwarp();
+}
+
 // Float64 clips (exact vertices) of the first `count` entries of S->gq.  Guarded pairs
 // are queued apart so that these rounds run with full warps.
 template <bool STATS, bool OCT, Acc A>
@@ -509,7 +639,9 @@ __device__ __forceinline__ void redo_round(const DepositParams &P, WarpSmem *S, 
 // Enumerate every (virtual tetrahedron, cell) pair of the 32 records in S (npairs:
 // this lane's pair count), 32 pairs per round: classify; deposit "cell inside"
 // pairs; queue partial pairs and clip them 32 at a time.
-template <bool STATS, bool OCT, Acc A>
+// COL: records below the guard are enumerated by column runs (one column clip per run);
+// otherwise, and for guarded records, by cells.
+template <bool STATS, bool OCT, Acc A, bool COL>
 __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, int lane, int npairs, Counters &cnt)
 {
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -535,30 +667,51 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                 for (int step = 16; step >= 1; step >>= 1)
                     if (S->start[t + step] <= idx && t + step < 32) t += step;
                 const int local = idx - S->start[t] + S->skip[t];
-                int ix, iy, iz;
-                decompose(local, S->dim[0][t], S->dim[1][t], ix, iy, iz);
-                const float cx = (float)(S->lo[0][t] + ix), cy = (float)(S->lo[1][t] + iy),
-                            cz = (float)(S->lo[2][t] + iz);
-                P3<float> n[4];
-                float e[4], ps[4], ng[4];
+                if (COL && !S->guard[t]) {
+                    int ia, ib, w, cx, cy, cz, kw;
+                    run_of(S, t, local, ia, ib, w, cx, cy, cz, kw);
+                    const int C = S->axis[t];
+                    const int cls = classify_run(S, t, C, (float)cx, (float)cy, (float)cz, kw);
+                    if (cls == CELL_INSIDE) {
+                        const double m = (double)S->rho[t];
+                        for (int j = 0; j < kw; ++j) {
+                            cnt.dep += m;
+                            if (!deposit_pair<OCT, A>(P, S, t, cx + (C == 0 ? j : 0), cy + (C == 1 ? j : 0),
+                                                      cz + (C == 2 ? j : 0), m) && STATS)
+                                cnt.dropped += m;
+                        }
+                        if (STATS) cnt.u[ST_INSIDE_CELLS] += kw;
+                    } else if (cls == CELL_PARTIAL) {
+                        ent = q_pack(t, ia, ib, w);
+                        partial = true;
+                    }
+                } else {
+                    int ix, iy, iz;
+                    decompose(local, S->dim[0][t], S->dim[1][t], ix, iy, iz);
+                    const float cx = (float)(S->lo[0][t] + ix), cy = (float)(S->lo[1][t] + iy),
+                                cz = (float)(S->lo[2][t] + iz);
+                    P3<float> n[4];
+                    float e[4], ps[4], ng[4];
 #pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
-                    e[f] = S->e[f][t];
-                    ps[f] = S->pos[f][t];
-                    ng[f] = S->neg[f][t];
-                }
-                const int cls = classify_cell<float>(n, e, ps, ng, cx, cy, cz);
-                if (cls == CELL_INSIDE) {
-                    const double m = (double)S->rho[t];
-                    cnt.dep += m;
-                    if (!deposit_pair<OCT, A>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) && STATS)
-                        cnt.dropped += m;
-                    if (STATS) cnt.u[ST_INSIDE_CELLS]++;
-                } else if (cls == CELL_PARTIAL) {
-                    ent = q_pack(t, ix, iy, iz);
-                    if (S->guard[t]) gpartial = true;
-                    else partial = true;
+                    for (int f = 0; f < 4; ++f) {
+                        n[f] = mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]);
+                        e[f] = S->e[f][t];
+                        ps[f] = S->pos[f][t];
+                        ng[f] = S->neg[f][t];
+                    }
+                    const int cls = classify_cell<float>(n, e, ps, ng, cx, cy, cz);
+                    if (cls == CELL_INSIDE) {
+                        const double m = (double)S->rho[t];
+                        cnt.dep += m;
+                        if (!deposit_pair<OCT, A>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) &&
+                            STATS)
+                            cnt.dropped += m;
+                        if (STATS) cnt.u[ST_INSIDE_CELLS]++;
+                    } else if (cls == CELL_PARTIAL) {
+                        ent = q_pack(t, ix, iy, iz);
+                        if (S->guard[t]) gpartial = true;
+                        else partial = true;
+                    }
                 }
             }
             const unsigned bal = __ballot_sync(kFull, partial);
@@ -572,7 +725,8 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
         const bool last = b0 + 32 >= total;
         if (qn >= 32 || (last && qn > 0)) {
             const int take = qn >= 32 ? 32 : qn;
-            clip_round<STATS, OCT, A>(P, S, take, lane, cnt);
+            if constexpr (COL) run_round<STATS, OCT, A>(P, S, take, lane, cnt);
+            else clip_round<STATS, OCT, A>(P, S, take, lane, cnt);
             if (lane < qn - take) S->q[lane] = S->q[take + lane];
             qn -= take;
             __syncwarp();

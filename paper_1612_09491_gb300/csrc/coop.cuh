@@ -34,9 +34,10 @@ __device__ __forceinline__ int chunk_setup(const DepositParams &P, WarpSmem *S, 
         if (P.chunk_start[mid] <= item) lo = mid;
         else hi = mid - 1;
     }
+    // q_cells holds the tetrahedron's pair count (column runs, or cells if guarded)
     const int64_t first = (item - P.chunk_start[lo]) * (int64_t)P.chunk_cells;
-    const int64_t ncell = P.q_cells[lo];
-    const int len = (int)min((int64_t)P.chunk_cells, ncell - first);
+    const int64_t npair = P.q_cells[lo];
+    const int len = (int)min((int64_t)P.chunk_cells, npair - first);
     if (lane != 0 || len <= 0) return 0;
     const int64_t id = P.q_tet[lo];
     P3<float> v[4], res[4];
@@ -53,8 +54,11 @@ __device__ __forceinline__ int chunk_setup(const DepositParams &P, WarpSmem *S, 
     }
     TetSetup<float> ts;
     if (tet_setup<float>(v, ts)) swap12(res);
+    if (!dims_fit_queue(ts.dim)) {
+        set_error(P.ws, 2, (int)(id & 0x7fffffff));
+        return 0;
+    }
     store_record(S, 0, ts, res, base, m_t, P.kappa_max, (int)first);
-    if (STATS) cnt.u[ST_BBOX_CELLS] += len;
     return len;
 }
 
@@ -170,11 +174,12 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                                     : (ncell > P.split_cells && ncell <= (int64_t)INT32_MAX))) {
                     // queued by the bin pass: its cells are done by the split work items
                     cnt.tgt += m_t;
-                    if (STATS) cnt.u[ST_BIN0 + size_bin(ncell)]++;
-                } else if (ncell > (int64_t)(1 << 25)) {
+                    if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
+                } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(ts.dim)) {
                     set_error(P.ws, 2, lane);  // 32 x 2^25 pairs still fit the int32 scan
                 } else {
-                    npairs = (int)ncell;
+                    // below the guard: column runs; guarded: cells (FP64 clips)
+                    npairs = (ts.kappa <= P.kappa_max) ? (int)run_count(ts.dim, ts.axis) : (int)ncell;
                     cnt.tgt += m_t;
                     if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
                     // the vertices' rounding residuals, needed only by guarded tetrahedra
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                 }
             }
             // ---- 2. pair enumeration and clips
-            coop_pairs<STATS, false, A>(P, S, lane, npairs, cnt);
+            coop_pairs<STATS, false, A, true>(P, S, lane, npairs, cnt);
             __syncwarp();
         }
     }

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
                         cnt.u[ts.vol6 == 0.0 ? ST_DEGENERATE : ST_SINGLE_CELL]++;
                         if (ts.vol6 != 0.0) { cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
                     }
-                } else if (ncell > (int64_t)(1 << 25)) {
+                } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(ts.dim)) {
                     set_error(P.ws, 2, (int)(t & 0x7fffffff));
                 } else {
                     npairs = (int)ncell;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
             }
         }
         __syncwarp();
-        coop_pairs<STATS, false, Acc::RUNTIME>(P, S, lane, npairs, cnt);
+        coop_pairs<STATS, false, Acc::RUNTIME, false>(P, S, lane, npairs, cnt);
         __syncwarp();
     }
     if (STATS) cnt.flush(P.ws);
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(128) k_bin_pass(const DepositParams P)
     for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n_tets; t0 += stride) {
         const int64_t t = t0 + lane;
         bool cand = false;
-        int64_t ncell = 0;
+        int64_t ncell = 0, npair = 0;
         float f[kNFeat];
         if (MODEL) {
 #pragma unroll
@@ -245,6 +245,8 @@ __global__ void __launch_bounds__(128) k_bin_pass(const DepositParams P)
                 tet_setup<float>(v, ts);
                 ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
                 cand = tet_ok(base, ts) && ts.vol6 != 0.0 && ncell > 1 && ncell <= (int64_t)INT32_MAX;
+                // the work items count pairs: column runs below the guard, cells above it
+                if (cand) npair = (ts.kappa <= P.kappa_max) ? run_count(ts.dim, ts.axis) : ncell;
                 if (MODEL && cand) tet_features(ts, f);
             }
         }
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(128) k_bin_pass(const DepositParams P)
                 const int64_t idx = (int64_t)b0 + __popc(bal & ((1u << lane) - 1u));
                 if (idx < P.q_cap) {
                     P.q_tet[idx] = t;
-                    P.q_cells[idx] = (int32_t)ncell;
+                    P.q_cells[idx] = (int32_t)npair;
                     if (MODEL) atomicOr(P.qbits + (t >> 5), 1u << (t & 31));
                 } else {
                     P.ws->queue_overflow = 1;

@@ -429,10 +429,10 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                           m_t);
                                 cnt.dep += m_t;
                                 if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; }
-                            } else if (ncell > (int64_t)(1 << 25)) {
+                            } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(dim)) {
                                 set_error(P.ws, 2, lane);
                             } else if (ncell > 0) {
-                                npairs = (int)ncell;
+                                npairs = (ts.kappa <= P.kappa_max) ? (int)run_count(dim, ts.axis) : (int)ncell;
                                 if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
 #pragma unroll
                                 for (int q = 0; q < 4; ++q) {
@@ -460,12 +460,17 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                 S->axis[lane] = ts.axis;
                                 S->guard[lane] = guard;
                                 S->skip[lane] = 0;
+                                {
+                                    const int C = ts.axis;
+                                    S->cut[lane] = (C == 0 ? lo[0] > ts.lo[0] : (C == 1 ? lo[1] > ts.lo[1] : lo[2] > ts.lo[2]))
+                                                       ? 1 : 0;
+                                }
                                 if (guard) store_residuals(S, lane, res);
                             }
                         }
                     }
                 }
-                coop_pairs<STATS, true, A>(P, S, lane, npairs, cnt);
+                coop_pairs<STATS, true, A, true>(P, S, lane, npairs, cnt);
                 __syncwarp();
             }
             __syncwarp();
