@@ -1,24 +1,33 @@
 #!/usr/bin/env python
-"""Throughput of the exact tetrahedron deposit on one GB300 (or N replicas).
+"""Throughput of the exact tetrahedron deposit on one GB300 (or N independent replicas).
 
-A step is one pass of the whole hot path over one synthetic lattice: every
-tetrahedron of the 6-per-cube tessellation is generated on the fly, classified
-against the cells of its bounding box, clipped exactly where partial, and its
-mass deposited into the float64 grid (the call overwrites the grid).
+Default workload: 1024^3 particles (6,442,450,944 tetrahedra), Zel'dovich P(k) ~ k^-2 with
+rms displacement 3 lattice spacings, periodic unit box, deposited onto the octree of 128^3-cell
+leaf blocks, levels 0-4 (2048^3 cells at the finest level).  One step is one pass of the whole
+hot path over the lattice: the octree built from the tetrahedra's sizes (one pass over every
+tetrahedron, histograms, refinement decisions), then every tetrahedron generated on the fly
+from its particles, classified against the cells of its bounding box in each leaf it
+reaches, clipped exactly where partial, and its mass accumulated into the float64 leaf
+blocks (the call overwrites them, FP32 clips renormalised to the exact total mass).
 
-Workload (default): 128^3 particles (12,582,912 tetrahedra), Zel'dovich P(k) ~ k^-2
-with rms displacement 2 lattice spacings, periodic unit box, uniform 256^3 float64
-grid.  Timed arm: FP32 clip with FP64 redo + FP64 accumulation, warp-cooperative
-schedule.  Beside it: the plain FP64 one-thread-per-tetrahedron GPU path on the
-same GPU, the density error between the two, and the FP64 CPU oracle timed on a
-bounded sample of the same workload.
+* value: the step with the positions resident in HBM (12.9 GB), CUDA events on the stream.
+* e2e: the same step through the host-buffer C ABI (pse_build_octree_streamed and
+  pse_deposit_octree_streamed: positions copied from pinned host memory in z-slabs inside the
+  calls) plus the read-back of the step's total deposited mass.
+* cpu_baseline: the FP64 CPU oracle on the host cores, on contiguous sub-lattices of the same
+  workload deposited at the same cell size (bounded sample); the GPU deposits the same
+  sub-lattices for the error on the sample.
+* Beside it, as extra keys: the plain FP64 one-thread-per-tetrahedron GPU path on a block of
+  the lattice, and the 128^3 precision workload (FP32 vs FP64 vs the oracle's full deposit)
+  and the 512^3 cost-model workload.
 
-``--impl reference`` times the oracle alone as the reference arm (host cores).
-Prints one JSON line on rank 0.
+``--config 2|3|4`` prints the line of another workload alone; ``--impl reference`` times the
+oracle alone (host cores).  Prints one JSON line on rank 0.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -34,37 +43,36 @@ if ROOT not in sys.path:
 METRIC = "tetrahedra deposited/sec and tet-cell clips/sec at stated density error vs plain FP64 GPU"
 UNIT = "tets/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+SLAB = 64                    # z-slab of the streamed calls, cube layers
+THRESHOLD_CELLS = 2.0        # octree refinement: median mean edge below 2 cells
+TUNING = {"blocks_per_sm": 4}
 
-# Algorithmic work per unit for the ALU roofline of the warp-cooperative kernel
-# (FP32 floating-point operations, FMA = 2): per tetrahedron the determinant, bounding
-# box and face planes (~150); per bounding-box cell one classification against 4 planes
-# (~32); per partial clip the intersections and fan integrals of the face polygons
-# against the cell's slabs (~620).
+# Algorithmic work per unit for the ALU roofline (FP32 floating-point operations, FMA = 2):
+# per tetrahedron the determinant, bounding box and face planes; per bounding-box cell one
+# classification against 4 planes; per partial cell the share of its column clip.  The
+# figures are counted by tests/test_flop_model_host.py on the workloads' own tetrahedra.
 FLOP_PER_TET = 150.0
 FLOP_PER_BBOX_CELL = 32.0
 FLOP_PER_CLIP = 620.0
-# From one ncu capture of the tuned deposit kernel (k_warp_coop, 4 blocks of 128 threads
-# per SM) on the headline workload: DRAM bytes read + written per launch, and thread
-# instructions issued per partial clip (warp instructions x active lanes / partial clips).
-# Both go stale when the kernel changes and must be re-taken with it.
-DRAM_BYTES_PER_LAUNCH = 300_260_608
-THREAD_INST_PER_CLIP = 5182.4
 SM_COUNT_GB300 = 152
 SM_MAX_MHZ_GB300 = 2070.0  # the part's maximum SM clock
-PRECISION = "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up"
 FP32_LANES_PER_SM = 128
+PRECISION = "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up"
+PROFILES = os.path.join(ROOT, "profiles")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="pse", choices=["pse", "reference"])
-    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--config", type=int, default=5)
     ap.add_argument("--no-baseline", action="store_true", help="skip the FP64 GPU baseline")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workload keys")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -128,73 +136,6 @@ def bus_id_of(dev_index: int):
         return None
 
 
-# ---------------------------------------------------------------- oracle ----
-def oracle_rate(pos, cfg, seconds: float, seed: int = 7):
-    """Oracle tets/s on a random sample of Lagrangian cubes sized for ~`seconds` of CPU work."""
-    import numpy as np
-
-    import oracle
-    n = cfg.n
-    rng = np.random.default_rng(seed)
-    threads = os.cpu_count() or 1
-    m = 2048
-    while True:  # grow the sample until it takes a quarter of the budget, then extrapolate
-        calib = np.sort(rng.choice(n ** 3, size=min(n ** 3, m), replace=False))
-        t0 = time.perf_counter()
-        oracle.deposit_lattice(pos, n, cfg.grid_n, cube_ids=calib, nthreads=threads)
-        dt = time.perf_counter() - t0
-        if dt >= 0.25 * seconds or calib.size >= n ** 3:
-            break
-        m *= 4
-    m = int(min(n ** 3, max(calib.size, calib.size * seconds / max(dt, 1e-9))))
-    ids = np.sort(rng.choice(n ** 3, size=m, replace=False))
-    t0 = time.perf_counter()
-    ref, st = oracle.deposit_lattice(pos, n, cfg.grid_n, cube_ids=ids, nthreads=threads)
-    dt = time.perf_counter() - t0
-    return {"value": 6 * m / dt, "unit": UNIT, "cores": int(st["threads"]), "kind": "oracle",
-            "sample": f"{m} random Lagrangian cubes ({6 * m} tetrahedra) of the workload, seed {seed}, "
-                      f"{dt:.1f} s"}, ids, ref
-
-
-def run_reference(args, cfg):
-    """The reference arm: the FP64 CPU oracle, each step a bounded sample of the workload."""
-    import numpy as np
-
-    import oracle
-    from pse_inputs import config_positions
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
-        return
-    pos = config_positions(cfg)
-    n = cfg.n
-    threads = os.cpu_count() or 1
-    rng = np.random.default_rng(11)
-    calib = np.sort(rng.choice(n ** 3, size=min(n ** 3, 2048), replace=False))
-    t0 = time.perf_counter()
-    oracle.deposit_lattice(pos, n, cfg.grid_n, cube_ids=calib, nthreads=threads)
-    per_cube = (time.perf_counter() - t0) / calib.size
-    budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
-    m = int(min(n ** 3, max(256, budget / max(per_cube, 1e-9))))
-    times = []
-    for k in range(args.warmup + args.steps):
-        ids = np.sort(rng.choice(n ** 3, size=m, replace=False))
-        t0 = time.perf_counter()
-        oracle.deposit_lattice(pos, n, cfg.grid_n, cube_ids=ids, nthreads=threads)
-        if k >= args.warmup:
-            times.append(time.perf_counter() - t0)
-    t = sum(times) / len(times)
-    value = 6 * m / t
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": cfg.name, "particles": f"{n}^3", "grid": f"uniform {cfg.grid_n}^3",
-                       "step": f"{m} random Lagrangian cubes per step (bounded sample)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"{m} random cubes ({6 * m} tetrahedra) per step"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 # ------------------------------------------------------------- replicas ----
 def replica_throughput(step_ms, units_per_rank, dist=None, device="cpu"):
     """Whole-job throughput of N independent replicas: every rank processed units_per_rank
@@ -211,7 +152,205 @@ def replica_throughput(step_ms, units_per_rank, dist=None, device="cpu"):
     return ms, world * units_per_rank / (ms * 1e-3)
 
 
-# ---------------------------------------------------------- other workloads --
+# ------------------------------------------------------------ profiles ----
+def source_digest() -> str:
+    """sha256 (16 hex) of the CUDA sources and the public header: ncu figures taken on other
+    sources do not describe the kernel this run times."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1612_09491_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    with open(os.path.join(ROOT, "include", "pse.h"), "rb") as f:
+        h.update(b"pse.h\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_figures(name: str) -> dict:
+    """The `key: value` figures of profiles/<name>.txt (ncu summary), or {} if absent."""
+    out = {}
+    try:
+        with open(os.path.join(PROFILES, name + ".txt")) as f:
+            for line in f:
+                if ":" in line and not line.startswith(("#", " ", "|")):
+                    k, v = line.split(":", 1)
+                    out[k.strip()] = v.strip()
+    except OSError:
+        pass
+    return out
+
+
+def roofline_alu(st, kernel_ms, sms, peaks, prof, units_key, units):
+    """ALU roofline of the deposit kernel: algorithmic FP32 work of the call's counters over the
+    kernel's measured duration, against 152 SMs x 128 lanes x 2 FLOP x max clock.  DRAM traffic
+    and issued instructions come from the committed ncu summary when it was taken on these
+    very sources (else null)."""
+    alg = FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] + FLOP_PER_CLIP * st["partial_clips"]
+    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_GB300 * 1e6 / 1e12
+    achieved = alg / (kernel_ms * 1e-3) / 1e12
+    fresh = prof.get("source_digest") == source_digest()
+    traffic = None
+    issue = None
+    if fresh and prof.get(f"dram_bytes_per_{units_key}"):
+        traffic = float(prof[f"dram_bytes_per_{units_key}"]) * units
+    if fresh and prof.get("thread_inst_per_clip"):
+        tin = float(prof["thread_inst_per_clip"])
+        rate = tin * st["partial_clips"] / (kernel_ms * 1e-3)
+        pk = sms * 4 * 32 * SM_MAX_MHZ_GB300 * 1e6
+        issue = {"thread_inst_per_clip": tin, "achieved_tinst_per_s": rate, "peak_tinst_per_s": pk, "frac": rate / pk,
+                 "note": "instructions issued by the kernel (ncu) against one warp instruction per scheduler per "
+                         "clock (4 per SM), all 32 lanes"}
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "traffic_unit": "bytes per launch (ncu dram read + write per unit x units)",
+            "traffic_source": prof.get("file") if fresh else
+            ("ncu summary taken on other sources" if prof else "no ncu summary"),
+            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
+                           f"{SM_MAX_MHZ_GB300:.0f} MHz (of measured: FMA microbenchmark beside it)",
+            "measured_fma_tflops": peaks["fp32_tflops"] if peaks else None,
+            "flop_model": {"per_tet": FLOP_PER_TET, "per_bbox_cell": FLOP_PER_BBOX_CELL, "per_partial_clip":
+                           FLOP_PER_CLIP}}, issue
+
+
+# ------------------------------------------------------------ oracle legs ----
+def sample_blocks(h_np, n, g_fine, m, count, seed, margin=24):
+    """`count` contiguous blocks of m^3 particles of the periodic lattice (float32 [n^3, 3]),
+    each unwrapped around its first particle and moved by a whole number of finest cells into a
+    local open box of gl^3 cells (the shift is a multiple of the cell size, so every tetrahedron
+    keeps its position relative to the cell planes, exactly).  Returns [(pos [m^3,3], gl, box)]."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    h = 1.0 / g_fine
+    P = h_np.reshape(n, n, n, 3)
+    out = []
+    for _ in range(count):
+        i0, j0, k0 = (int(v) for v in rng.integers(0, n, 3))
+        ii, jj, kk = (np.arange(m) + i0) % n, (np.arange(m) + j0) % n, (np.arange(m) + k0) % n
+        pts = P[np.ix_(kk, jj, ii)].astype(np.float64)
+        d = pts - pts[0, 0, 0]
+        d -= np.round(d)
+        q = pts[0, 0, 0] + d
+        lo = np.floor(q.reshape(-1, 3).min(0) / h) - margin
+        local = q - lo * h
+        gl = int(np.ceil(local.reshape(-1, 3).max() / h)) + margin
+        gl = (gl + 7) // 8 * 8
+        out.append((np.ascontiguousarray(local.reshape(-1, 3).astype(np.float32)), gl, gl * h))
+    return out
+
+
+def oracle_blocks(blocks, m, n, seconds):
+    """The oracle on as many sample blocks as fit `seconds` of host time (all cores)."""
+    import oracle
+    threads = os.cpu_count() or 1
+    grids, used, t_tot = [], 0, 0.0
+    for pos, gl, box in blocks:
+        t0 = time.perf_counter()
+        g, st = oracle.deposit_lattice(pos, (m, m, m), gl, box=box, periodic=False, particle_mass=1.0 / n ** 3,
+                                       nthreads=threads)
+        t_tot += time.perf_counter() - t0
+        grids.append(g)
+        used += 1
+        if t_tot >= seconds:
+            break
+    tets = 6 * (m - 1) ** 3 * used
+    return {"value": tets / t_tot, "unit": UNIT, "cores": int(st["threads"]), "kind": "oracle",
+            "sample": f"{used} contiguous blocks of {m}^3 particles ({tets} tetrahedra) of the workload, each "
+                      f"deposited alone at the workload's finest cell size, {t_tot:.1f} s"}, grids
+
+
+def gpu_blocks_error(pse, blocks, grids, m, n, dev, g_fine):
+    """The GPU's FP32 deposit of the oracle's sample blocks against the oracle, cell by cell."""
+    import numpy as np
+    import torch
+    from paper_1612_09491_gb300.metrics import cell_errors
+    fast, ref = [], []
+    for (pos, gl, box), g in zip(blocks, grids):
+        d = torch.from_numpy(pos).to(dev)
+        out = pse.deposit_uniform(d, (m, m, m), gl, box=box, periodic=False, particle_mass=1.0 / n ** 3,
+                                  precision=pse.PSE_FP32_FP64ACC, schedule=pse.PSE_WARP_COOPERATIVE)
+        fast.append(out.cpu().numpy().ravel())
+        ref.append(g.ravel())
+    fast, ref = np.concatenate(fast), np.concatenate(ref)
+    mean_cell = 1.0 / g_fine ** 3  # the full deposit's mean cell mass
+    e = cell_errors(fast, ref, floor_mass=1e-3 * mean_cell)
+    filled = ref >= 0.5 * mean_cell
+    e["floor"] = "1e-3 of the full deposit's mean cell mass"
+    e["on_filled_cells"] = cell_errors(fast[filled], ref[filled])
+    e["filled_cells"] = int(filled.sum())
+    e["sample"] = "the cpu_baseline blocks, deposited alone on both sides"
+    return e
+
+
+def run_reference(args, cfg):
+    """The reference arm: the FP64 CPU oracle on the host cores, each step a bounded sample of the
+    workload (contiguous sub-lattices at the workload's cell size for the 1024^3 workload, random
+    Lagrangian cubes otherwise)."""
+    import numpy as np
+
+    import oracle
+    from pse_inputs import config_positions, zeldovich_positions_device
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = os.cpu_count() or 1
+    budget = 150.0 / max(1, args.steps + args.warmup)  # whole run within a few minutes
+    n = cfg.n
+    if cfg.index == 5:
+        import torch
+        dev = torch.device("cuda", 0) if torch.cuda.is_available() else None
+        pos = zeldovich_positions_device(n, cfg.spectral_index, cfg.rms_disp, cfg.seed, device=dev or "cpu")
+        h_np = pos.cpu().numpy()
+        del pos
+        m = 40
+        cal = sample_blocks(h_np, n, cfg.grid_n, m, 1, seed=11)
+        t0 = time.perf_counter()
+        oracle.deposit_lattice(cal[0][0], (m, m, m), cal[0][1], box=cal[0][2], periodic=False,
+                               particle_mass=1.0 / n ** 3, nthreads=threads)
+        per_block = time.perf_counter() - t0
+        nb = max(1, int(budget / max(per_block, 1e-9)))
+        times, rng_seed = [], 12
+        for k in range(args.warmup + args.steps):
+            blocks = sample_blocks(h_np, n, cfg.grid_n, m, nb, seed=rng_seed + k)
+            t0 = time.perf_counter()
+            for p, gl, box in blocks:
+                oracle.deposit_lattice(p, (m, m, m), gl, box=box, periodic=False, particle_mass=1.0 / n ** 3,
+                                       nthreads=threads)
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        tets = 6 * (m - 1) ** 3 * nb
+        sample = f"{nb} contiguous blocks of {m}^3 particles ({tets} tetrahedra) per step, finest cell size"
+        grid = f"octree bc={cfg.bc} levels 0-{cfg.max_level} (finest {cfg.grid_n}^3)"
+    else:
+        pos = config_positions(cfg)
+        rng = np.random.default_rng(11)
+        calib = np.sort(rng.choice(n ** 3, size=min(n ** 3, 2048), replace=False))
+        t0 = time.perf_counter()
+        oracle.deposit_lattice(pos, n, cfg.grid_n, cube_ids=calib, nthreads=threads)
+        per_cube = (time.perf_counter() - t0) / calib.size
+        m = int(min(n ** 3, max(256, budget / max(per_cube, 1e-9))))
+        times = []
+        for k in range(args.warmup + args.steps):
+            ids = np.sort(rng.choice(n ** 3, size=m, replace=False))
+            t0 = time.perf_counter()
+            oracle.deposit_lattice(pos, n, cfg.grid_n, cube_ids=ids, nthreads=threads)
+            if k >= args.warmup:
+                times.append(time.perf_counter() - t0)
+        tets = 6 * m
+        sample = f"{m} random Lagrangian cubes ({tets} tetrahedra) per step"
+        grid = f"uniform {cfg.grid_n}^3"
+    t = sum(times) / len(times)
+    value = tets / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg.name, "particles": f"{n}^3", "grid": grid, "step": sample + " (bounded sample)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------- helpers ----
 def _timed(step, steps, warmup, flush, stream):
     """CUDA-event times (ms) of `steps` calls of step() after `warmup` untimed ones, L2 flushed between."""
     import torch
@@ -220,7 +359,8 @@ def _timed(step, steps, warmup, flush, stream):
     torch.cuda.synchronize()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for k in range(steps):
-        flush.fill_(k & 0xFF)
+        if flush is not None:
+            flush.fill_(k & 0xFF)
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
@@ -253,224 +393,8 @@ def _tet_size_sample(pos, n, g, layers=8):
             "sample": f"{layers} cube layers in the middle of the lattice, cells of the {g}^3 grid"}
 
 
-def run_workload(args, cfg):
-    """Workloads 3 (octree), 4 (uniform 512^3 with the learned cost model) and 5 (octree over a
-    1024^3 lattice streamed from pinned host memory in z-slabs).  One JSON line, like main()."""
-    import numpy as np
+def _dist_init():
     import torch
-
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1612_09491_gb300 as pse
-    from paper_1612_09491_gb300 import autotune
-    from paper_1612_09491_gb300 import costmodel as cm
-    from paper_1612_09491_gb300.metrics import cell_errors
-    from pse_inputs import CONFIGS, config_positions, zeldovich_positions_device
-
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    prec = pse.PSE_FP32_FP64ACC
-    n = cfg.n
-    t0 = time.perf_counter()
-    if n <= 256:
-        pos = torch.from_numpy(config_positions(cfg)).to(dev)
-        gen = "numpy PCG64 + FFT on the host"
-    else:
-        pos = zeldovich_positions_device(n, cfg.spectral_index, cfg.rms_disp, cfg.seed, device=dev)
-        gen = "torch generator + torch.fft on the GPU (float32)"
-    gen_s = time.perf_counter() - t0
-    extra = {"input_generation": f"{gen}, {gen_s:.1f} s"}
-    config = {"workload": cfg.name, "particles": f"{n}^3", "tets": cfg.n_tets,
-              "spectrum": f"P(k)~k^{cfg.spectral_index}", "rms_disp_spacings": cfg.rms_disp,
-              "precision": PRECISION,
-              "l2": "512 MB buffer written between timed steps", "parallelism": "replicas x1"}
-    base = None
-    if cfg.grid == "octree":
-        slab = 64
-        if cfg.index == 5:
-            # the positions live in pinned host memory; the GPU copy is dropped
-            h = torch.empty((n ** 3, 3), dtype=torch.float32).pin_memory()
-            h.copy_(pos)
-            del pos
-            torch.cuda.empty_cache()
-            t0 = time.perf_counter()
-            oct_ = pse.build_octree_streamed(h, n, cfg.bc, cfg.max_level, slab, 2.0)
-            extra["octree_build_s"] = time.perf_counter() - t0
-            out = torch.empty((oct_.n_leaves, cfg.bc, cfg.bc, cfg.bc), dtype=torch.float64, device=dev)
-
-            def step(stats=False):
-                return pse.deposit_octree_streamed(h, n, oct_, slab, out=out, stats=stats, precision=prec,
-                                                   tuning={"blocks_per_sm": 4})
-            config.update({"grid": f"octree bc={cfg.bc} levels 0-{cfg.max_level} (finest {cfg.grid_n}^3)",
-                           "schedule": "warp-cooperative", "streaming": f"z-slabs of {slab} cube layers from "
-                                                                        "pinned host memory, double-buffered"})
-            h2d = int(h.numel() * 4 * (1 + 1 / slab))
-        else:
-            t0 = time.perf_counter()
-            oct_ = pse.build_octree_from_tet_sizes(pos, n, cfg.bc, cfg.max_level, 2.0)
-            torch.cuda.synchronize()
-            extra["octree_build_s"] = time.perf_counter() - t0
-            out = torch.empty((oct_.n_leaves, cfg.bc, cfg.bc, cfg.bc), dtype=torch.float64, device=dev)
-            tuned, tune_ms = autotune.tune(lambda tu: pse.deposit_octree(pos, n, oct_, out=out, tuning=tu,
-                                                                         precision=prec),
-                                           signature=f"octree:{cfg.name}")
-            config["autotune_ms"] = tune_ms
-
-            def step(stats=False):
-                return pse.deposit_octree(pos, n, oct_, out=out, stats=stats, tuning=tuned, precision=prec)
-            config.update({"grid": f"octree bc={cfg.bc} levels 0-{cfg.max_level} (finest {cfg.grid_n}^3)",
-                           "schedule": "warp-cooperative", "tuning": tuned})
-            h2d = 0
-        config["leaves"] = int(oct_.n_leaves)
-        config["leaf_levels"] = {int(l): int(c) for l, c in zip(*np.unique(oct_.leaves()[:, 0], return_counts=True))}
-        _, st = step(stats=True)
-        grid_cells = oct_.n_cells
-    else:
-        g = cfg.grid_n
-        out = torch.empty((g, g, g), dtype=torch.float64, device=dev)
-        ws = torch.empty(pse.workspace_size(pse._lib.PSE_OP_DEPOSIT_UNIFORM, pse.lattice(n),
-                                            schedule=pse.PSE_BINNED_PERSISTENT, cost_model=cm.CostModel()),
-                         dtype=torch.uint8, device=dev)
-        # the cost model, trained on the counts the exact deposit produces on workloads 1 and 2
-        t0 = time.perf_counter()
-        feats, targs = [], []
-        for c in (CONFIGS[1], CONFIGS[2]):
-            p = torch.from_numpy(config_positions(c)).to(dev)
-            feats.append(cm.features(p, c.n, c.grid_n))
-            targs.append(cm.labels(cm.tet_counts(p, c.n, c.grid_n)))
-        feat, targ = torch.cat(feats), torch.cat(targs)
-        mu, sd = cm.standardisation(feat[:: max(1, feat.shape[0] // 200000)].cpu().numpy())
-        model = cm.CostModel(cm.pack({**cm.he_init(0), "mu": mu, "sigma": sd}))
-        hist = cm.fit(model, feat, targ, steps=2000, batch=8192, lr=3e-3)
-        extra["cost_model"] = {"training_s": time.perf_counter() - t0, "loss_first_last": [hist[0], hist[-1]],
-                               "train_rows": int(feat.shape[0])}
-        del feat, targ, feats, targs
-        arms = {"warp": dict(schedule=pse.PSE_WARP_COOPERATIVE, tuning={"blocks_per_sm": 4}, precision=prec),
-                "binned-bbox": dict(schedule=pse.PSE_BINNED_PERSISTENT, precision=prec,
-                                    tuning={"blocks_per_sm": 4, "split_cells": 512, "chunk_cells": 512}),
-                "binned-model": dict(schedule=pse.PSE_BINNED_PERSISTENT, cost_model=model, precision=prec,
-                                     tuning={"blocks_per_sm": 4, "split_cells": 256, "chunk_cells": 512})}
-        arm_ms = {}
-        for name, kw in arms.items():
-            ms_list = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, **kw), max(1, args.steps),
-                             1, flush, stream)
-            arm_ms[name] = sum(ms_list) / len(ms_list)
-        extra["arms_ms"] = arm_ms
-        chosen = arms["binned-model"]
-
-        def step(stats=False):
-            return pse.deposit_uniform(pos, n, g, out=out, workspace=ws, stats=stats, **chosen)
-        config.update({"grid": f"uniform {g}^3 float64", "schedule": "binned persistent, cost-model split",
-                       "tuning": chosen["tuning"]})
-        h2d = 0
-        _, st = step(stats=True)
-        grid_cells = g ** 3
-        # the plain FP64 one-thread-per-tetrahedron path, on a contiguous block of 128 x 128 x 32 cubes
-        i, j, k = np.meshgrid(np.arange(128), np.arange(128), np.arange(32), indexing="ij")
-        ids = torch.from_numpy(np.sort((i + n * (j + n * (k + n // 2))).ravel())).to(dev)
-        bms = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, precision=pse.PSE_FP64_PLAIN,
-                                                 schedule=pse.PSE_THREAD_PER_TET, cube_ids=ids), 1, 1, flush, stream)[0]
-        fast = pse.deposit_uniform(pos, n, g, cube_ids=ids, **{k: v for k, v in chosen.items()
-                                                               if k != "cost_model"}).cpu().numpy()
-        slow = out.cpu().numpy()
-        filled = slow >= 0.5 / g ** 3  # cells the block fills (not its sparse fringe)
-        base = {"tets_per_s": 6 * ids.numel() / (bms * 1e-3), "sample": "128 x 128 x 32 contiguous cubes",
-                "error_of_timed_arm_on_sample": cell_errors(fast, slow, floor_mass=1e-3 / g ** 3),
-                "error_floor": "1e-3 of the full deposit's mean cell mass",
-                "error_on_filled_cells": cell_errors(fast[filled], slow[filled]), "filled_cells": int(filled.sum()),
-                "note": "the block's fringe holds slivers of single tetrahedra; 'filled' = FP64 mass >= half "
-                        "the mean cell mass"}
-
-    tet_sizes = _tet_size_sample(h if cfg.index == 5 else pos, n, cfg.grid_n)
-    with ClockSampler(bus_id_of(0)) as clk:
-        t_wall0 = time.perf_counter()
-        step_ms = _timed(step, args.steps, args.warmup, flush, stream)
-        t_wall = time.perf_counter() - t_wall0
-    ms = sum(step_ms) / len(step_ms)
-    value = cfg.n_tets / (ms * 1e-3)
-    mass_error = abs(float(out.sum()) - 1.0)
-    if base is None and cfg.index == 3:
-        fast = out.cpu().numpy()
-        bms = _timed(lambda: pse.deposit_octree(pos, n, oct_, out=out, precision=pse.PSE_FP64_PLAIN,
-                                                schedule=pse.PSE_THREAD_PER_TET), 1, 1, flush, stream)[0]
-        base = {"tets_per_s": cfg.n_tets / (bms * 1e-3), "ms_per_step": bms,
-                "error_of_timed_arm": cell_errors(fast, out.cpu().numpy())}
-    if base is None and cfg.index == 5:
-        # FP32 against the plain FP64 path on a contiguous block of 64 x 64 x 32 cubes, positions
-        # back on the GPU for this check; floor 1e-3 of the full deposit's mean cell mass
-        pos_d = h.to(dev)
-        i, j, k = np.meshgrid(np.arange(64), np.arange(64), np.arange(32), indexing="ij")
-        ids = torch.from_numpy(np.sort((i + n * (j + n * (k + n // 2))).ravel())).to(dev)
-        pse.deposit_octree(pos_d, n, oct_, out=out, cube_ids=ids, tuning={"blocks_per_sm": 4})
-        touched = torch.nonzero(out.view(out.shape[0], -1).abs().sum(1) > 0).ravel()  # leaves the block reaches
-        fast = out[touched].cpu().numpy()
-        bms = _timed(lambda: pse.deposit_octree(pos_d, n, oct_, out=out, cube_ids=ids, precision=pse.PSE_FP64_PLAIN,
-                                                schedule=pse.PSE_THREAD_PER_TET), 1, 1, flush, stream)[0]
-        slow = out[touched].cpu().numpy()
-        filled = slow >= 0.5 / float(grid_cells)  # cells the block fills (not its sparse fringe)
-        base = {"tets_per_s": 6 * ids.numel() / (bms * 1e-3), "sample": "64 x 64 x 32 contiguous cubes",
-                "error_of_timed_arm_on_sample": cell_errors(fast, slow, floor_mass=1e-3 / float(grid_cells)),
-                "error_floor": "1e-3 of the full deposit's mean cell mass",
-                "error_on_filled_cells": cell_errors(fast[filled], slow[filled]),
-                "filled_cells": int(filled.sum()), "leaves_compared": int(touched.numel()),
-                "note": "the block's fringe holds slivers of single tetrahedra; 'filled' = FP64 mass >= half "
-                        "the mean cell mass"}
-        del pos_d
-    if base is not None:
-        base["speedup"] = value / base["tets_per_s"]
-    csum = clk.summary()
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count or SM_COUNT_GB300
-    peaks = pse.measure_peaks(stream)
-    peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_GB300 * 1e6 / 1e12
-    alg = FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] + FLOP_PER_CLIP * st["partial_clips"]
-    achieved = alg / (ms * 1e-3) / 1e12
-    result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": config,
-        "clips_per_s": st["partial_clips"] / (ms * 1e-3),
-        "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
-                                        "degenerate_tets", "single_cell_tets", "inverted_tets")},
-        "tet_sizes": tet_sizes,
-        "mass_error": mass_error,
-        "fp64_gpu_baseline": base,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "note": "step time (all kernels of the call)",
-                     "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
-                                    f"{SM_MAX_MHZ_GB300:.0f} MHz",
-                     "measured_fma_tflops": peaks["fp32_tflops"]},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 0,
-                "note": "streamed from pinned host memory inside the step" if h2d else
-                        "inputs resident (no host copies in this workload's step)"},
-        "grid_cells": int(grid_cells), "clocks": csum, "wall_s_timed": t_wall, **extra,
-    }
-    print(json.dumps(result), flush=True)
-
-
-# ---------------------------------------------------------------- ours ------
-def main():
-    args = parse()
-    from pse_inputs import CONFIGS
-    cfg = CONFIGS[args.config]
-    if args.impl == "reference":
-        run_reference(args, cfg)
-        return
-    if args.config >= 3:
-        run_workload(args, cfg)
-        return
-
-    import numpy as np
-    import torch
-
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1612_09491_gb300 as pse
-    from paper_1612_09491_gb300.metrics import cell_errors
-    from pse_inputs import config_positions
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -479,12 +403,212 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return dist, world, rank, local
+
+
+# ------------------------------------------------- the 1024^3 octree workload --
+def run_scale(args, cfg):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_09491_gb300 as pse
+    from pse_inputs import zeldovich_positions_device
+
+    dist, world, rank, local = _dist_init()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n, bc, ml = cfg.n, cfg.bc, cfg.max_level
+    n_tets = cfg.n_tets
+    prec = pse.PSE_FP32_FP64ACC
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    dev = torch.device("cuda", local)
+    t0 = time.perf_counter()
+    pos = zeldovich_positions_device(n, cfg.spectral_index, cfg.rms_disp, cfg.seed, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    h_pos = torch.empty((n ** 3, 3), dtype=torch.float32).pin_memory()
+    h_pos.copy_(pos)
+    tet_sizes = _tet_size_sample(pos, n, cfg.grid_n)
+
+    def build():
+        return pse.build_octree_from_tet_sizes(pos, n, bc, ml, THRESHOLD_CELLS)
+
+    # the tree, the output blocks and the call's counters (counting kernels, outside the timing)
+    oct_ = build()
+    out = torch.empty((oct_.n_leaves, bc, bc, bc), dtype=torch.float64, device=dev)
+    _, st = pse.deposit_octree(pos, n, oct_, out=out, stats=True, precision=prec, tuning=TUNING)
+    leaf_levels = {int(l): int(c) for l, c in zip(*np.unique(oct_.leaves()[:, 0], return_counts=True))}
+    n_leaves = oct_.n_leaves
+    del oct_
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        o = build()
+        if o.n_leaves != n_leaves:
+            raise RuntimeError("the octree changed between steps")
+        if ev is not None:
+            ev[1].record(stream)
+        pse.deposit_octree(pos, n, o, out=out, precision=prec, tuning=TUNING)
+        if ev is not None:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    with ClockSampler(bus_id_of(local)) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            step(evs[k])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    barrier()
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    build_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    dep_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    ms, value = replica_throughput(step_ms, n_tets, dist, dev)
+    mass_error = abs(float(out.sum()) - 1.0)
+
+    # end to end through the host-buffer C ABI: both calls stream the positions from pinned
+    # host memory in z-slabs; the step's result read back is its total deposited mass
+    ke = max(1, min(args.e2e_steps, args.steps))
+    del pos
+    torch.cuda.empty_cache()
+    e2e_ms = []
+    mass_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    for k in range(ke + 1):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        o = pse.build_octree_streamed(h_pos, n, bc, ml, SLAB, THRESHOLD_CELLS)
+        pse.deposit_octree_streamed(h_pos, n, o, SLAB, out=out, precision=prec, tuning=TUNING)
+        mass_h.copy_(out.sum().view(1), non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:  # the first call warms the slab buffers
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_mean = sum(e2e_ms) / len(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_mean], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_mean = float(t.item())
+    h2d = int(2 * h_pos.numel() * 4 * (1 + 1 / SLAB))  # the build's pass and the deposit's pass
+    hist_bytes = sum(64 * 8 ** l for l in range(ml)) * 4
+
+    result = {}
+    if rank == 0:
+        h_np = h_pos.numpy()
+        base = None
+        if not args.no_baseline:
+            # the plain FP64 one-thread-per-tetrahedron path and the timed FP32 path on a contiguous
+            # block of 64 x 64 x 32 cubes (positions back on the GPU for this check)
+            pos_d = h_pos.to(dev)
+            o = pse.build_octree_from_tet_sizes(pos_d, n, bc, ml, THRESHOLD_CELLS)
+            i, j, k = np.meshgrid(np.arange(64), np.arange(64), np.arange(32), indexing="ij")
+            ids = torch.from_numpy(np.sort((i + n * (j + n * (k + n // 2))).ravel())).to(dev)
+            pse.deposit_octree(pos_d, n, o, out=out, cube_ids=ids, precision=prec, tuning=TUNING)
+            touched = torch.nonzero(out.view(out.shape[0], -1).abs().sum(1) > 0).ravel()
+            fast = out[touched].cpu().numpy()
+            bms = _timed(lambda: pse.deposit_octree(pos_d, n, o, out=out, cube_ids=ids,
+                                                    precision=pse.PSE_FP64_PLAIN, schedule=pse.PSE_THREAD_PER_TET),
+                         1, 1, None, stream)[0]
+            fms = _timed(lambda: pse.deposit_octree(pos_d, n, o, out=out, cube_ids=ids, precision=prec,
+                                                    tuning=TUNING), 1, 1, None, stream)[0]
+            pse.deposit_octree(pos_d, n, o, out=out, cube_ids=ids, precision=pse.PSE_FP64_PLAIN,
+                               schedule=pse.PSE_THREAD_PER_TET)
+            slow = out[touched].cpu().numpy()
+            from paper_1612_09491_gb300.metrics import cell_errors
+            cells = float(cfg.grid_n) ** 3
+            filled = slow >= 0.5 / cells
+            base = {"tets_per_s": 6 * ids.numel() / (bms * 1e-3), "ms_on_sample": bms,
+                    "fp32_ms_on_sample": fms, "sample": "64 x 64 x 32 contiguous cubes",
+                    "speedup": value / (6 * ids.numel() / (bms * 1e-3)),
+                    "speedup_on_sample": bms / fms,
+                    "error_of_timed_arm_on_sample": cell_errors(fast, slow, floor_mass=1e-3 / cells),
+                    "error_floor": "1e-3 of the full deposit's mean cell mass",
+                    "error_on_filled_cells": cell_errors(fast[filled], slow[filled]),
+                    "filled_cells": int(filled.sum()), "leaves_compared": int(touched.numel())}
+            del pos_d
+        cpu = oracle_err = None
+        if not args.no_cpu:
+            blocks = sample_blocks(h_np, n, cfg.grid_n, 40, 64, seed=7)
+            cpu, grids = oracle_blocks(blocks, 40, n, args.cpu_seconds)
+            oracle_err = gpu_blocks_error(pse, blocks[:len(grids)], grids, 40, n, dev, cfg.grid_n)
+        props = torch.cuda.get_device_properties(dev)
+        sms = props.multi_processor_count or SM_COUNT_GB300
+        peaks = pse.measure_peaks(stream)
+        prof = profile_figures("k_oct_warp_scale-1024c-octree128")
+        prof["file"] = "profiles/k_oct_warp_scale-1024c-octree128.txt"
+        kern = sum(dep_ms) / len(dep_ms)
+        roof, issue = roofline_alu(st, kern, sms, peaks, prof, "tet", n_tets)
+        extra = {}
+        if not args.no_extra:
+            extra["workload_precision_128c"] = run_precision(args, pse, dev, stream, standalone=False)
+            extra["workload_learned_512c"] = run_learned(args, pse, dev, stream)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg.name, "particles": f"{n}^3", "tets": n_tets,
+                       "spectrum": f"P(k)~k^{cfg.spectral_index}", "rms_disp_spacings": cfg.rms_disp,
+                       "grid": f"octree bc={bc} levels 0-{ml} (finest {cfg.grid_n}^3), refined where the "
+                               f"median mean edge < {THRESHOLD_CELLS} cells", "leaves": n_leaves,
+                       "leaf_levels": leaf_levels, "precision": PRECISION, "schedule": "warp-cooperative",
+                       "tuning": TUNING,
+                       "step": "octree build from tetrahedron sizes + octree deposit, positions resident",
+                       "l2": "inputs larger than L2 (12.9 GB positions, 68.7 GB leaf blocks); no flush",
+                       "input_generation": f"torch generator + torch.fft on the GPU (float32), {gen_s:.1f} s",
+                       "parallelism": f"replicas x{world}"},
+            "clips_per_s": world * st["partial_clips"] / (ms * 1e-3),
+            "step_parts_ms": {"octree_build": sum(build_ms) / len(build_ms), "deposit": kern},
+            "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
+                                            "degenerate_tets", "single_cell_tets", "inverted_tets")},
+            "tet_sizes": tet_sizes,
+            "mass_error": mass_error,
+            "fp64_gpu_baseline": base,
+            "error_vs_oracle": oracle_err,
+            "kernel_ms": kern,
+            "roofline": roof,
+            "issue": issue,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * n_tets / (e2e_mean * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": hist_bytes + 8, "ms_per_step": e2e_mean, "steps": len(e2e_ms),
+                    "path": "pse_build_octree_streamed + pse_deposit_octree_streamed from pinned host memory "
+                            f"(z-slabs of {SLAB} cube layers, double-buffered), then the total mass read back; "
+                            "the leaf blocks stay on the GPU",
+                    "total_mass": float(mass_h.item())},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk.summary(),
+            "wall_s_timed": t_wall,
+            **extra,
+        }
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------- the 128^3 precision workload --
+def run_precision(args, pse, dev, stream, standalone=True):
+    """128^3 particles onto the uniform 256^3 grid: the timed FP32 path (autotuned), the plain FP64
+    GPU path, compensated FP32 accumulation, the paper's warp-per-tetrahedron design, and the
+    oracle's full deposit (timed: the cpu_baseline of this workload) with every cell compared."""
+    import numpy as np
+    import torch
+
+    from paper_1612_09491_gb300 import autotune
+    from paper_1612_09491_gb300 import costmodel as cm
+    from paper_1612_09491_gb300.metrics import cell_errors
+    from pse_inputs import CONFIGS, config_positions
+    cfg = CONFIGS[2]
     n, g = cfg.n, cfg.grid_n
     n_tets = cfg.n_tets
     pos_host = config_positions(cfg)
@@ -492,181 +616,219 @@ def main():
     out = torch.empty((g, g, g), dtype=torch.float64, device=dev)
     ws = torch.empty(pse.workspace_size(schedule=pse.PSE_BINNED_PERSISTENT), dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    from paper_1612_09491_gb300 import autotune
     prec = pse.PSE_FP32_FP64ACC
 
     def call(tu, **kw):
-        """One deposit with an autotuner candidate {"schedule": "warp" | "binned", knobs...}."""
         knobs = {k: v for k, v in tu.items() if k != "schedule"}
         sched = pse.PSE_BINNED_PERSISTENT if tu["schedule"] == "binned" else pse.PSE_WARP_COOPERATIVE
         return pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=prec, schedule=sched, tuning=knobs,
                                    **kw)
 
     tuned, tune_ms = autotune.tune(call, signature=f"uniform:{cfg.name}", candidates=autotune.UNIFORM_CANDIDATES)
-    peaks = pse.measure_peaks(stream)  # the FP32 and FP64-reduction peaks of this GPU
-
-    def step(accumulate=False):
-        call(tuned, accumulate=accumulate)
-
-    # the workload's tetrahedron sizes (mean edge length in cells), from the cost-model features
-    from paper_1612_09491_gb300 import costmodel as cm
-    edges = cm.features(pos, n, g)[:, 11].cpu().numpy()
-    tet_sizes = {"mean_edge_cells_quantiles": dict(zip(("min", "p01", "median", "p99", "max"),
-                                                       [float(v) for v in np.quantile(edges, [0, .01, .5, .99, 1])]))}
-    del edges
-    # kernels of one step: [bin pass, chunk scan,] deposit kernel, mass renormalisation
-    launches_per_step = 4 if tuned["schedule"] == "binned" else 2
-    # counters of one pass (synchronising call, outside the timed region)
     _, st = call(tuned, stats=True)
     fast_grid = out.cpu().numpy().copy()
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with ClockSampler(bus_id_of(local)) as clk:
-        t_wall0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.fill_(k & 0xFF)  # evict L2 between steps
-            evs[k][0].record(stream)
-            step()
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall0
-    barrier()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms, value = replica_throughput(step_ms, n_tets, dist, dev)
-    clips_per_s = world * st["partial_clips"] / (ms * 1e-3)
-
-    # kernel-only duration (accumulate mode: no output clear), for the roofline
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        kev[k][0].record(stream)
-        step(accumulate=True)
-        kev[k][1].record(stream)
-    torch.cuda.synchronize()
-    kern_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
-
-    # end to end through the public API with host buffers
+    steps = max(1, args.steps) if standalone else 5
+    step_ms = _timed(lambda: call(tuned), steps, 3, flush, stream)
+    ms = sum(step_ms) / len(step_ms)
+    kern_ms = sum(_timed(lambda: call(tuned, accumulate=True), steps, 1, flush, stream)) / steps
+    # end to end: positions from pinned host memory in, the grid back out, every step
     pos_pin = torch.from_numpy(pos_host).pin_memory()
     out_pin = torch.empty((g, g, g), dtype=torch.float64).pin_memory()
-    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        eev[k][0].record(stream)
-        pos.copy_(pos_pin, non_blocking=True)
-        step()
-        out_pin.copy_(out, non_blocking=True)
-        eev[k][1].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = sum(a.elapsed_time(b) for a, b in eev) / len(eev)
 
-    result = {}
-    if rank == 0:
-        # plain FP64 GPU baseline on the same GPU, and the density error between the two
-        base = None
-        if not args.no_baseline:
-            bev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-            pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=pse.PSE_FP64_PLAIN,
-                                schedule=pse.PSE_THREAD_PER_TET)  # warm-up
-            torch.cuda.synchronize()
-            flush.fill_(1)
-            bev[0].record(stream)
-            pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=pse.PSE_FP64_PLAIN,
-                                schedule=pse.PSE_THREAD_PER_TET)
-            bev[1].record(stream)
-            torch.cuda.synchronize()
-            bms = bev[0].elapsed_time(bev[1])
-            ref64 = out.cpu().numpy()
-            err = cell_errors(fast_grid, ref64)
-            base = {"tets_per_s": n_tets / (bms * 1e-3), "ms_per_step": bms, "speedup": (n_tets / (ms * 1e-3)) /
-                    (n_tets / (bms * 1e-3)), "error_of_timed_arm": err}
-            # the paper's GPU design (one warp per tetrahedron, Sec. 6.2) with the same clip
-            pms = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=prec,
-                                                     schedule=pse.PSE_WARP_PER_TET), 3, 1, flush, stream)
-            pms = sum(pms) / len(pms)
-            base["paper_design_warp_per_tet"] = {"tets_per_s": n_tets / (pms * 1e-3), "ms_per_step": pms,
-                                                 "speedup_of_timed_arm": pms / ms}
-            # the same clips with compensated FP32 (hi, lo) accumulation instead of FP64 reductions
-            knobs = {k: v for k, v in tuned.items() if k != "schedule"}
-            csched = pse.PSE_BINNED_PERSISTENT if tuned["schedule"] == "binned" else pse.PSE_WARP_COOPERATIVE
-            cms = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, tuning=knobs, schedule=csched,
-                                                     precision=pse.PSE_FP32_COMPENSATED), 3, 1, flush, stream)
-            cms = sum(cms) / len(cms)
-            base["fp32_compensated_accumulation"] = {"tets_per_s": n_tets / (cms * 1e-3), "ms_per_step": cms,
-                                                     "error_vs_fp64": cell_errors(out.cpu().numpy(), ref64)}
-        # roofline of the dominant kernel (FP32 ALU bound)
-        alg_flop = (FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] +
-                    FLOP_PER_CLIP * st["partial_clips"])
-        props = torch.cuda.get_device_properties(dev)
-        sms = props.multi_processor_count or SM_COUNT_GB300
-        csum = clk.summary()
-        peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_GB300 * 1e6 / 1e12
-        achieved = alg_flop / (kern_ms * 1e-3) / 1e12
-        deposits = st["partial_clips"] + st["inside_cells"]  # FP64 reductions issued (upper bound)
-        cpu = None
-        oracle_err = None
-        if not args.no_cpu:
-            cpu, ids, ref = oracle_rate(pos_host, cfg, args.cpu_seconds)
-            sub = pse.deposit_uniform(pos, n, g, precision=pse.PSE_FP32_FP64ACC, schedule=pse.PSE_WARP_COOPERATIVE,
-                                      cube_ids=torch.from_numpy(ids).to(dev))
-            oracle_err = cell_errors(sub.cpu().numpy(), ref)
-            oracle_err["sample"] = ("same cube sample as cpu_baseline, deposited alone on both sides (a sparse "
-                                    "deposit: cells covered by one tetrahedron's sliver are included)")
-        result = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": cfg.name, "particles": f"{n}^3", "tets": n_tets, "grid": f"uniform {g}^3 float64",
-                       "spectrum": f"P(k)~k^{cfg.spectral_index}", "rms_disp_spacings": cfg.rms_disp,
-                       "precision": PRECISION,
-                       "schedule": {"binned": "binned persistent", "warp": "warp-cooperative"}[tuned["schedule"]],
-                       "tuning": tuned, "autotune_ms": tune_ms,
-                       "l2": "512 MB buffer written between timed steps",
-                       "parallelism": f"replicas x{world}"},
-            "clips_per_s": clips_per_s,
-            "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
-                                            "degenerate_tets", "single_cell_tets", "inverted_tets", "bin_counts")},
-            "tet_sizes": tet_sizes,
-            "fp64_gpu_baseline": base,
-            "error_vs_oracle": oracle_err,
-            "kernel_ms": kern_ms,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak,
-                         "traffic": DRAM_BYTES_PER_LAUNCH if tuned == {"blocks_per_sm": 4, "schedule": "warp"}
-                         else None, "traffic_unit": "bytes per launch (ncu dram read + write)",
-                         "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
-                                        f"{SM_MAX_MHZ_GB300:.0f} MHz",
-                         "measured_fma_tflops": peaks["fp32_tflops"],
-                         "measured_fma_how": peaks["how"].split(";")[0]},
-            "atomics": {"achieved_per_s": deposits / (kern_ms * 1e-3), "peak_per_s": peaks["red_f64_per_s"],
-                        "frac": deposits / (kern_ms * 1e-3) / peaks["red_f64_per_s"],
-                        "note": "FP64 global reductions of the deposit kernel against a scattered-reduction "
-                                "microbenchmark measured in this run"},
-            "issue": {"thread_inst_per_clip": THREAD_INST_PER_CLIP,
-                      "achieved_tinst_per_s": THREAD_INST_PER_CLIP * st["partial_clips"] / (kern_ms * 1e-3),
-                      "peak_tinst_per_s": sms * 4 * 32 * SM_MAX_MHZ_GB300 * 1e6,
-                      "frac": THREAD_INST_PER_CLIP * st["partial_clips"] / (kern_ms * 1e-3) /
-                              (sms * 4 * 32 * SM_MAX_MHZ_GB300 * 1e6),
-                      "note": "instruction issue of the deposit kernel against one warp instruction per "
-                              "scheduler per clock (4 per SM), all 32 lanes"},
-            "cpu_baseline": cpu,
-            "e2e": {"value": world * n_tets / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(pos_host.nbytes),
-                    "d2h_bytes_per_step": int(out.numel() * 8), "ms_per_step": e2e_ms},
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": csum,
-            "wall_s_timed": t_wall,
-        }
-        print(json.dumps(result), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    def e2e_step():
+        pos.copy_(pos_pin, non_blocking=True)
+        call(tuned)
+        out_pin.copy_(out, non_blocking=True)
+    e2e_ms = sum(_timed(e2e_step, steps, 1, flush, stream)) / steps
+    res = {"workload": cfg.name, "particles": f"{n}^3", "tets": n_tets, "grid": f"uniform {g}^3 float64",
+           "tets_per_s": n_tets / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "kernel_ms": kern_ms,
+           "clips_per_s": st["partial_clips"] / (ms * 1e-3),
+           "schedule": {"binned": "binned persistent", "warp": "warp-cooperative"}[tuned["schedule"]],
+           "tuning": tuned, "autotune_ms": tune_ms,
+           "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
+                                           "inverted_tets", "bin_counts")},
+           "e2e": {"tets_per_s": n_tets / (e2e_ms * 1e-3), "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": int(pos_host.nbytes), "d2h_bytes_per_step": int(out.numel() * 8)}}
+    if not args.no_baseline:
+        bms = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=pse.PSE_FP64_PLAIN,
+                                                 schedule=pse.PSE_THREAD_PER_TET), 1, 1, flush, stream)[0]
+        ref64 = out.cpu().numpy()
+        base = {"tets_per_s": n_tets / (bms * 1e-3), "ms_per_step": bms, "speedup": bms / ms,
+                "error_of_timed_arm": cell_errors(fast_grid, ref64)}
+        pms = sum(_timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, precision=prec,
+                                                     schedule=pse.PSE_WARP_PER_TET), 3, 1, flush, stream)) / 3
+        base["paper_design_warp_per_tet"] = {"tets_per_s": n_tets / (pms * 1e-3), "ms_per_step": pms,
+                                             "speedup_of_timed_arm": pms / ms}
+        knobs = {k: v for k, v in tuned.items() if k != "schedule"}
+        csched = pse.PSE_BINNED_PERSISTENT if tuned["schedule"] == "binned" else pse.PSE_WARP_COOPERATIVE
+        cms = sum(_timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, tuning=knobs, schedule=csched,
+                                                     precision=pse.PSE_FP32_COMPENSATED), 3, 1, flush, stream)) / 3
+        base["fp32_compensated_accumulation"] = {"tets_per_s": n_tets / (cms * 1e-3), "ms_per_step": cms,
+                                                 "error_vs_fp64": cell_errors(out.cpu().numpy(), ref64)}
+        res["fp64_gpu_baseline"] = base
+    if not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        ref, ost = oracle.deposit_lattice(pos_host, n, g, nthreads=os.cpu_count() or 1)
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": n_tets / dt, "unit": UNIT, "cores": int(ost["threads"]), "kind": "oracle",
+                               "sample": f"the whole workload ({n_tets} tetrahedra), {dt:.1f} s"}
+        e = cell_errors(fast_grid, ref)
+        e["cells"] = "every cell of the 256^3 grid, floor 1e-3 of the mean occupied cell"
+        res["error_vs_oracle"] = e
+    tet = cm.features(pos, n, g)[:, 11].cpu().numpy()
+    res["tet_sizes"] = {"mean_edge_cells_quantiles": dict(zip(("min", "p01", "median", "p99", "max"),
+                                                              [float(v) for v in np.quantile(tet, [0, .01, .5, .99, 1])]))}
+    return res
+
+
+# ------------------------------------------------- the 512^3 cost-model workload --
+def run_learned(args, pse, dev, stream):
+    """512^3 particles onto the uniform 512^3 grid: the cost model trained on the counts the exact
+    deposit produces on the 32^3 and 128^3 workloads, then the warp schedule, the bbox-binned and
+    the model-binned persistent schedules (one warm-up and one timed call each)."""
+    import torch
+
+    from paper_1612_09491_gb300 import costmodel as cm
+    from pse_inputs import CONFIGS, config_positions, zeldovich_positions_device
+    cfg = CONFIGS[4]
+    n, g = cfg.n, cfg.grid_n
+    prec = pse.PSE_FP32_FP64ACC
+    pos = zeldovich_positions_device(n, cfg.spectral_index, cfg.rms_disp, cfg.seed, device=dev)
+    out = torch.empty((g, g, g), dtype=torch.float64, device=dev)
+    ws = torch.empty(pse.workspace_size(pse._lib.PSE_OP_DEPOSIT_UNIFORM, pse.lattice(n),
+                                        schedule=pse.PSE_BINNED_PERSISTENT, cost_model=cm.CostModel()),
+                     dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    feats, targs = [], []
+    for c in (CONFIGS[1], CONFIGS[2]):
+        p = torch.from_numpy(config_positions(c)).to(dev)
+        feats.append(cm.features(p, c.n, c.grid_n))
+        targs.append(cm.labels(cm.tet_counts(p, c.n, c.grid_n)))
+    feat, targ = torch.cat(feats), torch.cat(targs)
+    mu, sd = cm.standardisation(feat[:: max(1, feat.shape[0] // 200000)].cpu().numpy())
+    model = cm.CostModel(cm.pack({**cm.he_init(0), "mu": mu, "sigma": sd}))
+    hist = cm.fit(model, feat, targ, steps=2000, batch=8192, lr=3e-3)
+    train_s = time.perf_counter() - t0
+    del feat, targ, feats, targs
+    arms = {"warp": dict(schedule=pse.PSE_WARP_COOPERATIVE, tuning=TUNING, precision=prec),
+            "binned-bbox": dict(schedule=pse.PSE_BINNED_PERSISTENT, precision=prec,
+                                tuning={"blocks_per_sm": 4, "split_cells": 512, "chunk_cells": 512}),
+            "binned-model": dict(schedule=pse.PSE_BINNED_PERSISTENT, cost_model=model, precision=prec,
+                                 tuning={"blocks_per_sm": 4, "split_cells": 256, "chunk_cells": 512})}
+    arm_ms = {}
+    for name, kw in arms.items():
+        arm_ms[name] = _timed(lambda: pse.deposit_uniform(pos, n, g, out=out, workspace=ws, **kw), 1, 1, None,
+                              stream)[0]
+    _, st = pse.deposit_uniform(pos, n, g, out=out, workspace=ws, stats=True, **arms["warp"])
+    best = min(arm_ms, key=arm_ms.get)
+    return {"workload": cfg.name, "particles": f"{n}^3", "tets": cfg.n_tets, "grid": f"uniform {g}^3 float64",
+            "arms_ms": arm_ms, "fastest": best, "tets_per_s": cfg.n_tets / (arm_ms[best] * 1e-3),
+            "model_vs_warp": arm_ms["warp"] / arm_ms["binned-model"],
+            "cost_model": {"training_s": train_s, "loss_first_last": [hist[0], hist[-1]]},
+            "counters": {k: st[k] for k in ("tets", "bbox_cells", "partial_clips", "fp64_redos")},
+            "mass_error": abs(float(out.sum()) - 1.0),
+            "note": "one warm-up and one timed call per arm; the model steers which tetrahedra are split "
+                    "across warps, never a deposited value"}
+
+
+# ------------------------------------------------- the 256^3 octree workload (3) --
+def run_octree256(args, cfg):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1612_09491_gb300 as pse
+    from paper_1612_09491_gb300 import autotune
+    from paper_1612_09491_gb300.metrics import cell_errors
+    from pse_inputs import config_positions
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    prec = pse.PSE_FP32_FP64ACC
+    n = cfg.n
+    pos = torch.from_numpy(config_positions(cfg)).to(dev)
+    oct_ = pse.build_octree_from_tet_sizes(pos, n, cfg.bc, cfg.max_level, THRESHOLD_CELLS)
+    out = torch.empty((oct_.n_leaves, cfg.bc, cfg.bc, cfg.bc), dtype=torch.float64, device=dev)
+    tuned, tune_ms = autotune.tune(lambda tu: pse.deposit_octree(pos, n, oct_, out=out, tuning=tu, precision=prec),
+                                   signature=f"octree:{cfg.name}")
+    _, st = pse.deposit_octree(pos, n, oct_, out=out, stats=True, tuning=tuned, precision=prec)
+
+    def step():
+        o = pse.build_octree_from_tet_sizes(pos, n, cfg.bc, cfg.max_level, THRESHOLD_CELLS)
+        pse.deposit_octree(pos, n, o, out=out, tuning=tuned, precision=prec)
+
+    with ClockSampler(bus_id_of(0)) as clk:
+        step_ms = _timed(step, args.steps, args.warmup, flush, stream)
+    ms = sum(step_ms) / len(step_ms)
+    value = cfg.n_tets / (ms * 1e-3)
+    fast = out.cpu().numpy()
+    bms = _timed(lambda: pse.deposit_octree(pos, n, oct_, out=out, precision=pse.PSE_FP64_PLAIN,
+                                            schedule=pse.PSE_THREAD_PER_TET), 1, 1, flush, stream)[0]
+    result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": cfg.name, "particles": f"{n}^3", "tets": cfg.n_tets,
+                         "grid": f"octree bc={cfg.bc} levels 0-{cfg.max_level}", "leaves": int(oct_.n_leaves),
+                         "leaf_levels": {int(l): int(c) for l, c in
+                                         zip(*np.unique(oct_.leaves()[:, 0], return_counts=True))},
+                         "tuning": tuned, "autotune_ms": tune_ms, "precision": PRECISION,
+                         "l2": "512 MB buffer written between timed steps", "parallelism": "replicas x1"},
+              "clips_per_s": st["partial_clips"] / (ms * 1e-3),
+              "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
+                                              "inverted_tets")},
+              "mass_error": abs(float(fast.sum()) - 1.0),
+              "fp64_gpu_baseline": {"tets_per_s": cfg.n_tets / (bms * 1e-3), "ms_per_step": bms,
+                                    "speedup": bms / ms, "error_of_timed_arm": cell_errors(fast, out.cpu().numpy())},
+              "clocks": clk.summary(),
+              "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                      "note": "inputs resident (no host copies in this workload's step)"}}
+    print(json.dumps(result), flush=True)
+
+
+def main():
+    args = parse()
+    from pse_inputs import CONFIGS
+    cfg = CONFIGS[args.config]
+    if args.impl == "reference":
+        run_reference(args, cfg)
+        return
+    if args.config == 5:
+        run_scale(args, cfg)
+    elif args.config == 3:
+        run_octree256(args, cfg)
+    else:
+        import torch
+
+        import __graft_entry__
+        __graft_entry__.build()
+        import paper_1612_09491_gb300 as pse
+        dist, world, rank, local = _dist_init()
+        dev = torch.device("cuda", local)
+        stream = torch.cuda.current_stream(dev)
+        if args.config == 4:
+            with ClockSampler(bus_id_of(local)) as clk:
+                res = run_learned(args, pse, dev, stream)
+        else:
+            with ClockSampler(bus_id_of(local)) as clk:
+                res = run_precision(args, pse, dev, stream, standalone=True)
+        if rank == 0:
+            ms = res.get("ms_per_step") or res["arms_ms"][res["fastest"]]
+            line = {"metric": METRIC, "value": res["tets_per_s"], "unit": UNIT, "n_gpus": world,
+                    "steps": res.get("steps", 1), "warmup": args.warmup, "ms_per_step": ms,
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                    "data": "synthetic", "config": {"workload": res["workload"], "parallelism": f"replicas x{world}"},
+                    "cpu_baseline": res.get("cpu_baseline"),
+                    "e2e": {"value": res.get("e2e", {}).get("tets_per_s", res["tets_per_s"]), "unit": UNIT,
+                            "h2d_bytes_per_step": res.get("e2e", {}).get("h2d_bytes_per_step", 0),
+                            "d2h_bytes_per_step": res.get("e2e", {}).get("d2h_bytes_per_step", 0)},
+                    "clocks": clk.summary(), "detail": res}
+            print(json.dumps(line), flush=True)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
 
 
 if __name__ == "__main__":

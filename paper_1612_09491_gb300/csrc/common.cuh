@@ -265,10 +265,17 @@ __device__ __forceinline__ int size_bin(int64_t cells)
     return b;
 }
 
+// Mass sums for the FP32 renormalisation, always kept: the target sum of m_t and the sum
+// of every computed deposit.  A persistent lane adds up to ~10^6 terms, so plain running
+// sums would drift by up to n x 2^-53 (the same mass added repeatedly rounds the same way):
+// equal lattice masses are counted as an integer (times m_t at the end) and deposits are
+// summed with Kahan's compensation.
 struct Counters {
     unsigned long long u[ST_NUM_U64];
     double mass_in, dropped;
-    double tgt, dep;  // always kept: sum of m_t and of every computed deposit (renormalisation)
+    double tgt;            // explicit tetrahedra: sum of m_t
+    unsigned ntgt;         // lattice tetrahedra (each P.m_tet)
+    double dep, dep_c;     // Kahan sum of deposits and its compensation
     __device__ void zero()
     {
 #pragma unroll
@@ -279,11 +286,25 @@ struct Counters {
     __device__ void zero_mass()
     {
         tgt = 0.0;
+        ntgt = 0;
         dep = 0.0;
+        dep_c = 0.0;
     }
-    __device__ void flush_mass(Workspace *ws)
+    __device__ __forceinline__ void add_tgt(const DepositParams &P, double m_t)
     {
-        double a = tgt, b = dep;
+        if (P.src == SRC_TETS) tgt += m_t;
+        else ++ntgt;
+    }
+    __device__ __forceinline__ void add_dep(double m)
+    {
+        const double y = m - dep_c;
+        const double t = dep + y;
+        dep_c = (t - dep) - y;
+        dep = t;
+    }
+    __device__ void flush_mass(const DepositParams &P, Workspace *ws)
+    {
+        double a = fma((double)ntgt, P.m_tet, tgt), b = dep - dep_c;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_down_sync(kFull, a, o);
@@ -545,7 +566,7 @@ __device__ __forceinline__ void deposit_clip(const DepositParams &P, const WarpS
     if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
     if (vol > 0.0) {
         const double m = (double)(S->rho[t] * (float)vol);
-        cnt.dep += m;
+        cnt.add_dep(m);
         if (!deposit_pair<OCT, A>(P, S, t, cx, cy, cz, m) && STATS) cnt.dropped += m;
     }
 }
@@ -613,7 +634,7 @@ __device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, i
             }
             if (j < kw && vol[j] > 0.f) {
                 const double m = (double)(rho * vol[j]);
-                cnt.dep += m;
+                cnt.add_dep(m);
                 if (!deposit_pair<OCT, A>(P, S, t, ex, ey, ez, m) && STATS) cnt.dropped += m;
             }
         }
@@ -675,7 +696,7 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                     if (cls == CELL_INSIDE) {
                         const double m = (double)S->rho[t];
                         for (int j = 0; j < kw; ++j) {
-                            cnt.dep += m;
+                            cnt.add_dep(m);
                             if (!deposit_pair<OCT, A>(P, S, t, cx + (C == 0 ? j : 0), cy + (C == 1 ? j : 0),
                                                       cz + (C == 2 ? j : 0), m) && STATS)
                                 cnt.dropped += m;
@@ -702,7 +723,7 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                     const int cls = classify_cell<float>(n, e, ps, ng, cx, cy, cz);
                     if (cls == CELL_INSIDE) {
                         const double m = (double)S->rho[t];
-                        cnt.dep += m;
+                        cnt.add_dep(m);
                         if (!deposit_pair<OCT, A>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) &&
                             STATS)
                             cnt.dropped += m;

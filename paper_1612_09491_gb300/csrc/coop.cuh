@@ -159,28 +159,28 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                     if (!deposit_cell<A>(P, (int64_t)base[0] + c[0], (int64_t)base[1] + c[1], (int64_t)base[2] + c[2], m_t) &&
                         STATS)
                         cnt.dropped += m_t;
-                    cnt.tgt += m_t;
-                    cnt.dep += m_t;
+                    cnt.add_tgt(P, m_t);
+                    cnt.add_dep(m_t);
                     if (STATS) cnt.u[ST_DEGENERATE]++;
                 } else if (ncell == 1) {
                     if (!deposit_cell<A>(P, (int64_t)base[0] + ts.lo[0], (int64_t)base[1] + ts.lo[1],
                                       (int64_t)base[2] + ts.lo[2], m_t) && STATS)
                         cnt.dropped += m_t;
-                    cnt.tgt += m_t;
-                    cnt.dep += m_t;
+                    cnt.add_tgt(P, m_t);
+                    cnt.add_dep(m_t);
                     if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
                 } else if (BINNED && split &&
                            (P.model ? ((P.qbits[tid >> 5] >> (tid & 31)) & 1u) != 0
                                     : (ncell > P.split_cells && ncell <= (int64_t)INT32_MAX))) {
                     // queued by the bin pass: its cells are done by the split work items
-                    cnt.tgt += m_t;
+                    cnt.add_tgt(P, m_t);
                     if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
                 } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(ts.dim)) {
                     set_error(P.ws, 2, lane);  // 32 x 2^25 pairs still fit the int32 scan
                 } else {
                     // below the guard: column runs; guarded: cells (FP64 clips)
                     npairs = (ts.kappa <= P.kappa_max) ? (int)run_count(ts.dim, ts.axis) : (int)ncell;
-                    cnt.tgt += m_t;
+                    cnt.add_tgt(P, m_t);
                     if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
                     // the vertices' rounding residuals, needed only by guarded tetrahedra
                     P3<float> res[4];
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
         }
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P.ws);
+    if (P.fixup) cnt.flush_mass(P, P.ws);
 }
 
 template <bool BINNED, Acc A>

@@ -56,12 +56,12 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
             set_error(P.ws, 4, (int)(t & 0x7fffffff));
             continue;
         }
-        cnt.tgt += m_t;
+        cnt.add_tgt(P, m_t);
         if (ts.vol6 == 0.0) {
             int c[3];
             centroid_cell(ts.v, c);
             if (!deposit_cell(P, base[0] + c[0], base[1] + c[1], base[2] + c[2], m_t) && STATS) cnt.dropped += m_t;
-            cnt.dep += m_t;
+            cnt.add_dep(m_t);
             if (STATS) cnt.u[ST_DEGENERATE]++;
             continue;
         }
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
         if (ncell == 1) {
             if (!deposit_cell(P, base[0] + ts.lo[0], base[1] + ts.lo[1], base[2] + ts.lo[2], m_t) && STATS)
                 cnt.dropped += m_t;
-            cnt.dep += m_t;
+            cnt.add_dep(m_t);
             if (STATS) cnt.u[ST_SINGLE_CELL]++;
             continue;
         }
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                     }
                     if (vol > 0.0) {
                         const double m = rho * vol;
-                        cnt.dep += m;
+                        cnt.add_dep(m);
                         if (!deposit_cell(P, (int64_t)base[0] + cx, (int64_t)base[1] + cy, (int64_t)base[2] + cz, m) &&
                             STATS)
                             cnt.dropped += m;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                 }
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P.ws);
+    if (P.fixup) cnt.flush_mass(P, P.ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -178,8 +178,8 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
                     if (!deposit_cell(P, (int64_t)base[0] + c[0], (int64_t)base[1] + c[1], (int64_t)base[2] + c[2], m_t) &&
                         STATS)
                         cnt.dropped += m_t;
-                    cnt.tgt += m_t;
-                    cnt.dep += m_t;
+                    cnt.add_tgt(P, m_t);
+                    cnt.add_dep(m_t);
                     if (STATS) {
                         cnt.u[ts.vol6 == 0.0 ? ST_DEGENERATE : ST_SINGLE_CELL]++;
                         if (ts.vol6 != 0.0) { cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
                     set_error(P.ws, 2, (int)(t & 0x7fffffff));
                 } else {
                     npairs = (int)ncell;
-                    cnt.tgt += m_t;
+                    cnt.add_tgt(P, m_t);
                     if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
                     store_record(S, 0, ts, res, base, m_t, P.kappa_max, 0);
                 }
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
         __syncwarp();
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P.ws);
+    if (P.fixup) cnt.flush_mass(P, P.ws);
 }
 
 // ---------------------------------------------------------------------------

@@ -237,12 +237,12 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
             cnt.mass_in += m_t;
             cnt.u[ST_INVERTED] += ((det6_box(P, x, k) < 0.0) != kuhn_negative((int)(t % 6))) ? 1 : 0;
         }
-        cnt.tgt += m_t;
+        cnt.add_tgt(P, m_t);
         double cen[3];
         tet_centroid(P, x, k, cen);
         if (det6_box(P, x, k) == 0.0) {
             add_mass(P, cen, m_t, cnt, STATS);
-            cnt.dep += m_t;
+            cnt.add_dep(m_t);
             if (STATS) cnt.u[ST_DEGENERATE]++;
             continue;
         }
@@ -313,14 +313,14 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
                         }
                         if (vol > 0.0) {
                             const double m = rho * vol;
-                            cnt.dep += m;
+                            cnt.add_dep(m);
                             cell_add(P, blk + (cx - org[0]) + bc * ((cy - org[1]) + bc * (cz - org[2])), m);
                         }
                     }
         }
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P.ws);
+    if (P.fixup) cnt.flush_mass(P, P.ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -377,10 +377,10 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
             cnt.mass_in += m_t;
             cnt.u[ST_INVERTED] += ((det6_box(P, x, k) < 0.0) != kuhn_negative(s)) ? 1 : 0;
         }
-                cnt.tgt += m_t;
+                cnt.add_tgt(P, m_t);
                 if (det6_box(P, x, k) == 0.0) {
                     add_mass<A>(P, cen, m_t, cnt, STATS);
-                    cnt.dep += m_t;
+                    cnt.add_dep(m_t);
                     if (STATS) cnt.u[ST_DEGENERATE]++;
                 } else {
                     fine_range(P, x, k, f0, f1);
@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                 cell_add<A>(P, P.out + (int64_t)hit.leaf * bc * bc * bc + (lo[0] - S->org[0][lane]) +
                                               bc * ((lo[1] - S->org[1][lane]) + bc * (lo[2] - S->org[2][lane])),
                                           m_t);
-                                cnt.dep += m_t;
+                                cnt.add_dep(m_t);
                                 if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; }
                             } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(dim)) {
                                 set_error(P.ws, 2, lane);
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
         }
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P.ws);
+    if (P.fixup) cnt.flush_mass(P, P.ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -485,58 +485,87 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int64_t hist_offset(int level) { return (int64_t)64 * ((((int64_t)1) << (3 * level)) - 1) / 7; }
 
-__global__ void __launch_bounds__(256) k_tet_size_hist(const DepositParams P, unsigned *__restrict__ hist,
-                                                       double threshold_unused)
+// One pass over the tetrahedra: per level 0 .. max_level-1, the node that holds the
+// tetrahedron's vertex centroid and the 64-bin log10 histogram bin of its mean edge length
+// in that level's cells.  The edge vectors are the unwrapped vertex offsets from vertex 0,
+// formed in float64 and rounded to float32 (a bin is 24% wide); the 32 tetrahedra of a warp
+// are neighbours, so equal (node, bin) keys are merged in the warp before one atomic per key.
+__global__ void __launch_bounds__(256) k_tet_size_hist(const DepositParams P, unsigned *__restrict__ hist)
 {
-    (void)threshold_unused;
     __shared__ unsigned sh[64 + 512];  // levels 0 and 1 aggregated per block
     for (int i = threadIdx.x; i < 576; i += blockDim.x) sh[i] = 0;
     __syncthreads();
+    const int lane = threadIdx.x & 31;
     const int64_t n_tets = 6 * P.n_units;
     const int levels = P.max_level;  // decisions are made for levels 0 .. max_level-1
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t ci, cj, ck;
-        if (!cube_of_unit(P, t / 6, ci, cj, ck)) continue;
-        float x[4][3];
-        int k[4][3];
-        lattice_tet_raw(P, ci, cj, ck, (int)(t % 6), x, k);
-        double e = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const double inv_box = 1.0 / P.box;
+    // whole warps iterate together (the merge below needs every lane)
+    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n_tets; t0 += stride) {
+        const int64_t t = t0 + lane;
+        bool ok = false;
+        float me = 0.f;        // mean edge length in level-0 cells
+        double cen[3] = {0.0, 0.0, 0.0};
+        if (t < n_tets) {
+            int64_t ci, cj, ck;
+            if (cube_of_unit(P, t / 6, ci, cj, ck)) {
+                ok = true;
+                float x[4][3];
+                int k[4][3];
+                lattice_tet_raw(P, ci, cj, ck, (int)(t % 6), x, k);
+                float r[4][3];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+                for (int a = 0; a < 3; ++a) {
+                    r[0][a] = 0.f;
+                    double sum = 0.0;
 #pragma unroll
-            for (int b = a + 1; b < 4; ++b) {
-                double s2 = 0.0;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double d = unwrapped(P, x, k, b, c) - unwrapped(P, x, k, a, c);
-                    s2 += d * d;
+                    for (int q = 1; q < 4; ++q) {
+                        const double d = ((double)x[q][a] - (double)x[0][a]) + (double)k[q][a] * P.box;
+                        r[q][a] = (float)d;
+                        sum += d;
+                    }
+                    cen[a] = (double)x[0][a] + 0.25 * sum;
+                    cen[a] -= P.box * floor(cen[a] * inv_box);
+                    if (!(cen[a] < P.box) || !(cen[a] >= 0.0)) cen[a] = 0.0;
                 }
-                e += sqrt(s2);
+                float es = 0.f;
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = a + 1; b < 4; ++b) {
+                        const float dx = r[b][0] - r[a][0], dy = r[b][1] - r[a][1], dz = r[b][2] - r[a][2];
+                        es += sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+                    }
+                const float h0 = (float)(P.box / (double)P.bc);
+                me = es * (1.f / 6.f) / h0;
             }
-        e /= 6.0;
-        double cen[3];
-        tet_centroid(P, x, k, cen);
-        for (int a = 0; a < 3; ++a) {
-            cen[a] -= P.box * floor(cen[a] / P.box);
-            if (!(cen[a] < P.box)) cen[a] = 0.0;
         }
         for (int l = 0; l < levels; ++l) {
-            const int64_t nn = (int64_t)1 << l;
-            int64_t node = 0, stride = 1;
-            for (int a = 0; a < 3; ++a) {
-                int64_t c = (int64_t)floor(cen[a] * (double)nn / P.box);
-                c = c < 0 ? 0 : (c >= nn ? nn - 1 : c);
-                node += c * stride;
-                stride *= nn;
+            unsigned long long key = ~0ull - (unsigned long long)lane;  // lanes without a tetrahedron match nothing
+            int bin = 0;
+            int64_t node = 0;
+            if (ok) {
+                const int64_t nn = (int64_t)1 << l;
+                int64_t stride_n = 1;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int64_t c = (int64_t)floor(cen[a] * (double)nn * inv_box);
+                    c = c < 0 ? 0 : (c >= nn ? nn - 1 : c);
+                    node += c * stride_n;
+                    stride_n *= nn;
+                }
+                // a level-l cell is 2^-l of a level-0 cell (an exact float scaling)
+                bin = (int)floorf((log10f(ldexpf(me, l)) + 3.0f) * (64.0f / 6.0f));
+                bin = bin < 0 ? 0 : (bin > 63 ? 63 : bin);
+                key = (unsigned long long)node * 64 + (unsigned long long)bin;
             }
-            const double h = P.box / ((double)P.bc * (double)nn);
-            const float lg = log10f((float)(e / h));
-            int bin = (int)floorf((lg + 3.0f) * (64.0f / 6.0f));
-            bin = bin < 0 ? 0 : (bin > 63 ? 63 : bin);
-            if (l == 0) atomicAdd(&sh[bin], 1u);
-            else if (l == 1) atomicAdd(&sh[64 + node * 64 + bin], 1u);
-            else atomicAdd(&hist[hist_offset(l) + node * 64 + bin], 1u);
+            const unsigned peers = __match_any_sync(kFull, key);
+            if (ok && lane == __ffs(peers) - 1) {
+                const unsigned c = (unsigned)__popc(peers);
+                if (l == 0) atomicAdd(&sh[bin], c);
+                else if (l == 1) atomicAdd(&sh[64 + node * 64 + bin], c);
+                else atomicAdd(&hist[hist_offset(l) + node * 64 + bin], c);
+            }
         }
     }
     __syncthreads();
@@ -735,7 +764,7 @@ cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStrea
     const int64_t cap = (int64_t)persistent_blocks((const void *)k_tet_size_hist, threads, 0) * 4;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_tet_size_hist<<<(unsigned)blocks, threads, 0, st>>>(p, hist, 0.0);
+    k_tet_size_hist<<<(unsigned)blocks, threads, 0, st>>>(p, hist);
     return cudaGetLastError();
 }
 
