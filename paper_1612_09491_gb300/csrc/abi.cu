@@ -336,7 +336,7 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
             // statistics and mass sums run over all slabs; the work counter and the binned
             // schedule's queue state restart with every slab
             r = stream_slabs(h_pos, p, slab_cubes, s, [&](pse::DepositParams &q, cudaStream_t ss) -> int {
-                cudaError_t e2 = cudaMemsetAsync(&q.ws->work_counter, 0, sizeof(q.ws->work_counter), ss);
+                cudaError_t e2 = cudaMemsetAsync(&q.ws->work_counter, 0, 2 * sizeof(q.ws->work_counter), ss);
                 if (e2 == cudaSuccess)
                     e2 = cudaMemsetAsync(&q.ws->queue_count, 0,
                                          sizeof(pse::Workspace) - offsetof(pse::Workspace, queue_count), ss);

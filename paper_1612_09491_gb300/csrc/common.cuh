@@ -599,7 +599,9 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
     __syncwarp();
 }
 
-// Column clips of the first `count` entries of S->q (runs of unguarded tetrahedra).
+// Column clips of the first `count` entries of S->q (runs of unguarded tetrahedra), one run
+// per lane.  (Dealing the (run, face) jobs and the level fans out over the warp raised the
+// active lanes but cost more in shuffles and reloads than it saved: 12% slower.)
 template <bool STATS, bool OCT, Acc A>
 __device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
 {
@@ -657,14 +659,25 @@ __device__ __forceinline__ void redo_round(const DepositParams &P, WarpSmem *S, 
     __syncwarp();
 }
 
-// Enumerate every (virtual tetrahedron, cell) pair of the 32 records in S (npairs:
-// this lane's pair count), 32 pairs per round: classify; deposit "cell inside"
-// pairs; queue partial pairs and clip them 32 at a time.
-// COL: records below the guard are enumerated by column runs (one column clip per run);
-// otherwise, and for guarded records, by cells.
-template <bool STATS, bool OCT, Acc A, bool COL>
+// Which records a kernel holds, and so which clips it carries:
+//  * kPassAll: records on both sides of the guard, enumerated by cells; FP32 clips and FP64
+//    clips in the same kernel (the warp-per-tetrahedron baseline);
+//  * kPassFp32: records below the guard only, enumerated by column runs (FP32 column clips);
+//  * kPassGuard: guarded records only, enumerated by cells (FP64 clips from the exact
+//    vertices).
+// The warp-cooperative and octree schedules run kPassFp32 and then kPassGuard over the same
+// tetrahedra, so neither kernel carries the other's clip code or registers.
+enum { kPassAll = 0, kPassFp32 = 1, kPassGuard = 2 };
+
+// Enumerate every (virtual tetrahedron, cell or run) pair of the 32 records in S (npairs:
+// this lane's pair count), 32 pairs per round: classify; deposit "cell inside" pairs; queue
+// partial pairs and clip them 32 at a time.
+template <bool STATS, bool OCT, Acc A, int PASS>
 __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, int lane, int npairs, Counters &cnt)
 {
+    constexpr bool COL = PASS == kPassFp32;
+    constexpr bool HAS_Q = PASS != kPassGuard;
+    constexpr bool HAS_GQ = PASS != kPassFp32;
     const unsigned lt_mask = (1u << lane) - 1u;
     int incl = npairs;
 #pragma unroll
@@ -688,7 +701,7 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                 for (int step = 16; step >= 1; step >>= 1)
                     if (S->start[t + step] <= idx && t + step < 32) t += step;
                 const int local = idx - S->start[t] + S->skip[t];
-                if (COL && !S->guard[t]) {
+                if constexpr (COL) {
                     int ia, ib, w, cx, cy, cz, kw;
                     run_of(S, t, local, ia, ib, w, cx, cy, cz, kw);
                     const int C = S->axis[t];
@@ -730,34 +743,42 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                         if (STATS) cnt.u[ST_INSIDE_CELLS]++;
                     } else if (cls == CELL_PARTIAL) {
                         ent = q_pack(t, ix, iy, iz);
-                        if (S->guard[t]) gpartial = true;
+                        if (PASS == kPassGuard || (PASS == kPassAll && S->guard[t])) gpartial = true;
                         else partial = true;
                     }
                 }
             }
-            const unsigned bal = __ballot_sync(kFull, partial);
-            if (partial) S->q[qn + __popc(bal & lt_mask)] = ent;
-            qn += __popc(bal);
-            const unsigned gbal = __ballot_sync(kFull, gpartial);
-            if (gpartial) S->gq[gn + __popc(gbal & lt_mask)] = ent;
-            gn += __popc(gbal);
+            if constexpr (HAS_Q) {
+                const unsigned bal = __ballot_sync(kFull, partial);
+                if (partial) S->q[qn + __popc(bal & lt_mask)] = ent;
+                qn += __popc(bal);
+            }
+            if constexpr (HAS_GQ) {
+                const unsigned gbal = __ballot_sync(kFull, gpartial);
+                if (gpartial) S->gq[gn + __popc(gbal & lt_mask)] = ent;
+                gn += __popc(gbal);
+            }
             __syncwarp();
         }
         const bool last = b0 + 32 >= total;
-        if (qn >= 32 || (last && qn > 0)) {
-            const int take = qn >= 32 ? 32 : qn;
-            if constexpr (COL) run_round<STATS, OCT, A>(P, S, take, lane, cnt);
-            else clip_round<STATS, OCT, A>(P, S, take, lane, cnt);
-            if (lane < qn - take) S->q[lane] = S->q[take + lane];
-            qn -= take;
-            __syncwarp();
+        if constexpr (HAS_Q) {
+            if (qn >= 32 || (last && qn > 0)) {
+                const int take = qn >= 32 ? 32 : qn;
+                if constexpr (COL) run_round<STATS, OCT, A>(P, S, take, lane, cnt);
+                else clip_round<STATS, OCT, A>(P, S, take, lane, cnt);
+                if (lane < qn - take) S->q[lane] = S->q[take + lane];
+                qn -= take;
+                __syncwarp();
+            }
         }
-        if (gn >= 32 || (last && gn > 0)) {
-            const int take = gn >= 32 ? 32 : gn;
-            redo_round<STATS, OCT, A>(P, S, take, lane, cnt);
-            if (lane < gn - take) S->gq[lane] = S->gq[take + lane];
-            gn -= take;
-            __syncwarp();
+        if constexpr (HAS_GQ) {
+            if (gn >= 32 || (last && gn > 0)) {
+                const int take = gn >= 32 ? 32 : gn;
+                redo_round<STATS, OCT, A>(P, S, take, lane, cnt);
+                if (lane < gn - take) S->gq[lane] = S->gq[take + lane];
+                gn -= take;
+                __syncwarp();
+            }
         }
         if (last && qn == 0 && gn == 0) break;
     }

@@ -23,7 +23,7 @@ namespace {
 // Split work item `item` of the binned schedule: chunk [first, first + len) of the
 // bounding-box cells of one queued tetrahedron, set up by lane 0 as record 0.  Returns
 // the lane's pair count (len on lane 0, else 0).
-template <bool STATS>
+template <bool STATS, int PASS>
 __device__ __forceinline__ int chunk_setup(const DepositParams &P, WarpSmem *S, int lane, int64_t item, int64_t q,
                                            Counters &cnt)
 {
@@ -58,15 +58,22 @@ __device__ __forceinline__ int chunk_setup(const DepositParams &P, WarpSmem *S, 
         set_error(P.ws, 2, (int)(id & 0x7fffffff));
         return 0;
     }
+    // each pass takes the pieces of its own side of the guard
+    const bool guard = !(ts.kappa <= P.kappa_max);
+    if (guard != (PASS == kPassGuard)) return 0;
     store_record(S, 0, ts, res, base, m_t, P.kappa_max, (int)first);
     return len;
 }
 
 constexpr int kCoopThreads = 128;
 
-template <bool STATS, int MINB, bool BINNED, Acc A>
+// PASS kPassFp32 visits every tetrahedron: it counts them, deposits the degenerate and
+// single-cell ones, and clips those below the guard by column runs.  PASS kPassGuard visits
+// them again and clips only the guarded multi-cell ones, cell by cell in FP64.
+template <bool STATS, int MINB, bool BINNED, Acc A, int PASS>
 __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositParams P)
 {
+    constexpr bool FIRST = PASS == kPassFp32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
     bind_residuals(P, S);
@@ -87,7 +94,7 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
 
     for (;;) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(&P.ws->work_counter, 1ull);
+        if (lane == 0) item = atomicAdd(FIRST ? &P.ws->work_counter : &P.ws->work_counter2, 1ull);
         item = __shfl_sync(kFull, item, 0);
         const bool is_chunk = BINNED && (int64_t)item < n_chunks;
         if (!is_chunk) {
@@ -128,7 +135,7 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
             int npairs = 0;
             double m_t = 0.0;
             if (is_chunk) {
-                npairs = chunk_setup<STATS>(P, S, lane, (int64_t)item, q, cnt);
+                npairs = chunk_setup<STATS, PASS>(P, S, lane, (int64_t)item, q, cnt);
                 __syncwarp();
             } else if (unit >= 0) {
                 P3<float> v[4];
@@ -145,14 +152,17 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                 }
                 TetSetup<float> ts;
                 const bool swapped = tet_setup<float>(v, ts);
-                if (STATS) {
+                if (STATS && FIRST) {
                     cnt.u[ST_TETS]++;
                     cnt.mass_in += m_t;
                     cnt.u[ST_INVERTED] += (swapped != (P.src != SRC_TETS && kuhn_negative(s))) ? 1 : 0;
                 }
                 const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
+                const bool guard = !(ts.kappa <= P.kappa_max);
                 if (!tet_ok(base, ts)) {
                     set_error(P.ws, 4, lane);
+                } else if (!FIRST && (ts.vol6 == 0.0 || ncell == 1 || !guard)) {
+                    // the guarded pass: nothing to do for this tetrahedron
                 } else if (ts.vol6 == 0.0) {
                     int c[3];
                     centroid_cell(ts.v, c);
@@ -173,31 +183,36 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                            (P.model ? ((P.qbits[tid >> 5] >> (tid & 31)) & 1u) != 0
                                     : (ncell > P.split_cells && ncell <= (int64_t)INT32_MAX))) {
                     // queued by the bin pass: its cells are done by the split work items
-                    cnt.add_tgt(P, m_t);
-                    if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
+                    if (FIRST) {
+                        cnt.add_tgt(P, m_t);
+                        if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
+                    }
                 } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(ts.dim)) {
                     set_error(P.ws, 2, lane);  // 32 x 2^25 pairs still fit the int32 scan
-                } else {
-                    // below the guard: column runs; guarded: cells (FP64 clips)
-                    npairs = (ts.kappa <= P.kappa_max) ? (int)run_count(ts.dim, ts.axis) : (int)ncell;
+                } else if (FIRST) {
                     cnt.add_tgt(P, m_t);
                     if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
-                    // the vertices' rounding residuals, needed only by guarded tetrahedra
-                    P3<float> res[4];
+                    if (!guard) {  // guarded ones are left to the second pass
+                        npairs = (int)run_count(ts.dim, ts.axis);
+                        P3<float> res[4];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) res[q] = mk<float>(0.f, 0.f, 0.f);
-                    if (!(ts.kappa <= P.kappa_max)) {
-                        P3<float> v2[4];
-                        int b2[3];
-                        if (P.src == SRC_TETS) explicit_tet<float>(P, unit, v2, b2, res);
-                        else lattice_tet<float>(P, ci, cj, ck, s, v2, b2, res);
-                        if (swapped) swap12(res);
+                        for (int q = 0; q < 4; ++q) res[q] = mk<float>(0.f, 0.f, 0.f);
+                        store_record(S, lane, ts, res, base, m_t, P.kappa_max, 0);
                     }
+                } else {
+                    // guarded: cells, clipped in FP64 from the exact vertices (the float32
+                    // vertices plus their rounding residuals)
+                    npairs = (int)ncell;
+                    P3<float> res[4], v2[4];
+                    int b2[3];
+                    if (P.src == SRC_TETS) explicit_tet<float>(P, unit, v2, b2, res);
+                    else lattice_tet<float>(P, ci, cj, ck, s, v2, b2, res);
+                    if (swapped) swap12(res);
                     store_record(S, lane, ts, res, base, m_t, P.kappa_max, 0);
                 }
             }
             // ---- 2. pair enumeration and clips
-            coop_pairs<STATS, false, A, true>(P, S, lane, npairs, cnt);
+            coop_pairs<STATS, false, A, PASS>(P, S, lane, npairs, cnt);
             __syncwarp();
         }
     }
@@ -205,8 +220,9 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
     if (P.fixup) cnt.flush_mass(P, P.ws);
 }
 
-template <bool BINNED, Acc A>
-cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, int64_t max_items, cudaStream_t st)
+template <bool BINNED, Acc A, int PASS>
+cudaError_t launch_coop_pass(const DepositParams &p, bool stats, int blocks_per_sm, int64_t max_items,
+                             cudaStream_t st)
 {
     // blocks_per_sm resident blocks of 128 threads: 2 (255 registers per thread, 8 warps per
     // SM), 3 (170 registers, 12 warps) or 4 (128 registers, 16 warps).  The counting
@@ -214,10 +230,10 @@ cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, i
     const int threads = kCoopThreads;
     const size_t smem = sizeof(WarpSmem) * (threads / 32);
     const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
-    const void *k = stats ? (const void *)k_warp_coop<true, 2, BINNED, A>
-                    : minb == 4 ? (const void *)k_warp_coop<false, 4, BINNED, A>
-                    : minb == 3 ? (const void *)k_warp_coop<false, 3, BINNED, A>
-                                : (const void *)k_warp_coop<false, 2, BINNED, A>;
+    const void *k = stats ? (const void *)k_warp_coop<true, 2, BINNED, A, PASS>
+                    : minb == 4 ? (const void *)k_warp_coop<false, 4, BINNED, A, PASS>
+                    : minb == 3 ? (const void *)k_warp_coop<false, 3, BINNED, A, PASS>
+                                : (const void *)k_warp_coop<false, 2, BINNED, A, PASS>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);
@@ -226,6 +242,15 @@ cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, i
     if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
     void *args[] = {const_cast<DepositParams *>(&p)};
     return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
+}
+
+// The FP32 pass, then the guarded pass over the same tetrahedra, on one stream.
+template <bool BINNED, Acc A>
+cudaError_t launch_coop(const DepositParams &p, bool stats, int blocks_per_sm, int64_t max_items, cudaStream_t st)
+{
+    cudaError_t e = launch_coop_pass<BINNED, A, kPassFp32>(p, stats, blocks_per_sm, max_items, st);
+    if (e != cudaSuccess) return e;
+    return launch_coop_pass<BINNED, A, kPassGuard>(p, stats, blocks_per_sm, max_items, st);
 }
 
 }  // namespace

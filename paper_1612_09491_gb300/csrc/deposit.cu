@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
             }
         }
         __syncwarp();
-        coop_pairs<STATS, false, Acc::RUNTIME, false>(P, S, lane, npairs, cnt);
+        coop_pairs<STATS, false, Acc::RUNTIME, kPassAll>(P, S, lane, npairs, cnt);
         __syncwarp();
     }
     if (STATS) cnt.flush(P.ws);

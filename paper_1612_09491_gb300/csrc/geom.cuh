@@ -801,12 +801,149 @@ PSE_HD float level_fan(const float2 *E, float c, float ox, float oy)
     return g;
 }
 
-// The tetrahedron of column_volumes given as arrays (clip frame, relative to the run).
+// The tetrahedron of a run given as arrays (clip frame, relative to the run's first cell).
 struct TetArrays {
     const P3<float> *p, *n;
     PSE_HD P3<float> vtx(int i) const { return p[i]; }
     PSE_HD P3<float> nrm(int f) const { return n[f]; }
 };
+
+// The local frame of one run: origin q (the centroid held in the run and rounded to 1/256,
+// so the cell planes and the levels c_j = j - q.z stay exact), the reference plane l(x, y) =
+// l0 + lx x + ly y held inside the run's z range at the column centre, the run length K and
+// the first level evaluated, j0 (0 if the tetrahedron may reach below the run, else 1).
+struct RunFrame {
+    float qx, qy, qz, l0, lx, ly;
+    int K, j0;
+};
+
+template <class Src>
+PSE_HD RunFrame run_frame(const Src &src, float lx, float ly, int K, bool lo_open)
+{
+    using T = float;
+    const P3<T> p0 = src.vtx(0), p1 = src.vtx(1), p2 = src.vtx(2), p3 = src.vtx(3);
+    const T cx = T(0.25) * ((p0.x + p1.x) + (p2.x + p3.x));
+    const T cy = T(0.25) * ((p0.y + p1.y) + (p2.y + p3.y));
+    const T cz = T(0.25) * ((p0.z + p1.z) + (p2.z + p3.z));
+    const T kf = (T)K;
+    RunFrame F;
+    F.qx = floor(fmin(fmax(cx, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256);
+    F.qy = floor(fmin(fmax(cy, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256);
+    F.qz = floor(fmin(fmax(cz, T(0)), kf) * T(256) + T(0.5)) * T(1.0 / 256);
+    const T xc = T(0.5) - F.qx, yc = T(0.5) - F.qy;
+    const T lc = fmin(fmax((cz - F.qz) + lx * (xc - (cx - F.qx)) + ly * (yc - (cy - F.qy)), -F.qz), kf - F.qz);
+    F.l0 = lc - lx * xc - ly * yc;
+    F.lx = lx;
+    F.ly = ly;
+    F.K = K;
+    F.j0 = lo_open ? 0 : 1;
+    return F;
+}
+
+// Whether face f can reach the run's column (its projection's bounding box meets the column
+// and it is not vertical).
+template <class Src>
+PSE_HD bool face_meets_column(const Src &src, int f, const RunFrame &F)
+{
+    using T = float;
+    int ia, ib, ic;
+    face_vertices(f, ia, ib, ic);
+    const P3<T> a = src.vtx(ia), b = src.vtx(ib), c = src.vtx(ic);
+    const T mnx = fmin(a.x, fmin(b.x, c.x)) - F.qx, mxx = fmax(a.x, fmax(b.x, c.x)) - F.qx;
+    const T mny = fmin(a.y, fmin(b.y, c.y)) - F.qy, mxy = fmax(a.y, fmax(b.y, c.y)) - F.qy;
+    if (mxx < -F.qx || mnx >= T(1) - F.qx || mxy < -F.qy || mny >= T(1) - F.qy) return false;
+    return src.nrm(f).z != T(0);
+}
+
+// One face of a run: the x and y slab passes (the clipped polygon is left in the 7 slots of
+// E), then 6 x its term of B(c_j) for the levels j0 .. K by the closed forms (a level the
+// face straddles gets the "below" form m6; the fan of its part above the level is subtracted
+// afterwards, see level_fan), its z range, its moment, and the straddled levels jlo .. jhi
+// (empty when jlo > jhi) with the plane data their fans need.
+template <int KW>
+struct FaceRun {
+    float k6[KW + 1];
+    float zmin, zmax, m6;
+    int jlo, jhi;
+    float nx, ny, nz, ef;  // face plane n . x = ef in the local frame
+};
+
+template <int KW, class Src>
+PSE_HD void face_run(const Src &src, int f, const RunFrame &F, float2 *E, FaceRun<KW> &R)
+{
+    using T = float;
+    int ia, ib, ic;
+    face_vertices(f, ia, ib, ic);
+    const P3<T> q = mk<T>(F.qx, F.qy, F.qz);
+    const P3<T> a = sub(src.vtx(ia), q), b = sub(src.vtx(ib), q), c = sub(src.vtx(ic), q);
+    const P3<T> nf = src.nrm(f);
+    const T mnx = fmin(a.x, fmin(b.x, c.x)), mxx = fmax(a.x, fmax(b.x, c.x));
+    const T mny = fmin(a.y, fmin(b.y, c.y)), mxy = fmax(a.y, fmax(b.y, c.y));
+    const T mnz = fmin(a.z, fmin(b.z, c.z)), mxz = fmax(a.z, fmax(b.z, c.z));
+    const T cmag = fmax(T(1), fmax(fmax(fmax(fabs(mnx), fabs(mxx)), fmax(fabs(mny), fabs(mxy))),
+                                   fmax(fabs(mnz), fabs(mxz))));
+    const T tol = T(8) * roundoff<T>() * cmag;
+    const T ef = dot(nf, a);
+    const T sc = fdiv(ef, dot(nf, nf));
+    const P3<T> o = mk<T>(sc * nf.x, sc * nf.y, sc * nf.z);
+    const T fo = o.z - fmaT(F.lx, o.x, fmaT(F.ly, o.y, F.l0));
+
+    slot_store(E, 0, a, b);
+    slot_store(E, 1, b, c);
+    slot_store(E, 2, c, a);
+    slab_pass<0>(E, -F.qx, T(1) - F.qx, tol);
+    FaceSums I;
+    yslab_sums(E, -F.qy, T(1) - F.qy, tol, o, fo, F.l0, F.lx, F.ly, I);
+
+    // levels the polygon straddles: jlo .. jhi (c_j - zmin > 0 and zmax - c_j > 0)
+    const T kf = (T)F.K;
+    const T flo = fmin(fmax(floor(I.zmin + F.qz) + T(1), T(F.j0)), kf + T(1));
+    const T fhi = fmin(fmax(ceil(I.zmax + F.qz) - T(1), T(-1)), kf);
+    R.jlo = (int)flo;
+    R.jhi = (int)fhi;
+    // closed forms: below jlo the face is above the level; from jlo on it is (at first taken
+    // as) below it
+#pragma unroll
+    for (int j = 0; j <= KW; ++j) {
+        const T cj = (T)j - F.qz;
+        const T v = (j < R.jlo) ? fmaT(T(3) * cj, I.x2, -I.y6) : I.m6;
+        R.k6[j] = (j >= F.j0 && j <= F.K) ? v : T(0);
+    }
+    R.zmin = I.zmin;
+    R.zmax = I.zmax;
+    R.m6 = I.m6;
+    R.nx = nf.x;
+    R.ny = nf.y;
+    R.nz = nf.z;
+    R.ef = ef;
+}
+
+// The anchor of a level fan: the point of the face plane at height c nearest the local
+// origin in the xy plane.
+PSE_HD void fan_anchor(float nx, float ny, float nz, float ef, float c, float &ox, float &oy)
+{
+    const float s = fmaT(-nz, c, ef) * fdiv(1.0f, fmaT(nx, nx, ny * ny));
+    ox = s * nx;
+    oy = s * ny;
+}
+
+// Cell volumes of a run from the level sums S[j] = 6 B(c_j): levels at or below the
+// tetrahedron's lowest point in the column hold exactly 0, and levels at or above its highest
+// point the column's whole volume, so they are set so rather than left to the rounding of
+// terms that cancel; then vol_j = (S[j+1] - S[j]) / 6.
+template <int KW>
+PSE_HD void column_finish(const RunFrame &F, float (&S)[KW + 1], float colmin, float colmax, float msum,
+                          float (&vol)[KW])
+{
+    using T = float;
+#pragma unroll
+    for (int j = 0; j <= KW; ++j) {
+        const T cj = (T)j - F.qz;
+        S[j] = (cj <= colmin) ? T(0) : ((cj >= colmax) ? msum : S[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < KW; ++j) vol[j] = (S[j + 1] - S[j]) * T(1.0 / 6.0);
+}
 
 // Overlap volumes of a positively oriented tetrahedron (clip frame, relative to the first
 // cell of the run: the run is [0,1)^2 x [0,K), K <= KW) with the K cells of the run.  src
@@ -818,93 +955,34 @@ template <int KW, class Src>
 PSE_HD void column_volumes(const Src &src, float lx, float ly, int K, bool lo_open, float (&vol)[KW], float2 *E)
 {
     using T = float;
-    T cx, cy, cz;
-    {
-        const P3<T> p0 = src.vtx(0), p1 = src.vtx(1), p2 = src.vtx(2), p3 = src.vtx(3);
-        cx = T(0.25) * ((p0.x + p1.x) + (p2.x + p3.x));
-        cy = T(0.25) * ((p0.y + p1.y) + (p2.y + p3.y));
-        cz = T(0.25) * ((p0.z + p1.z) + (p2.z + p3.z));
-    }
-    const T kf = (T)K;
-    // local frame: the centroid held in the run and rounded to 1/256, so levels stay exact
-    const P3<T> q = mk<T>(floor(fmin(fmax(cx, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256),
-                          floor(fmin(fmax(cy, T(0)), T(1)) * T(256) + T(0.5)) * T(1.0 / 256),
-                          floor(fmin(fmax(cz, T(0)), kf) * T(256) + T(0.5)) * T(1.0 / 256));
-    const T xlo = -q.x, xhi = T(1) - q.x, ylo = -q.y, yhi = T(1) - q.y;
-    const T xc = T(0.5) - q.x, yc = T(0.5) - q.y;
-    const T lc = fmin(fmax((cz - q.z) + lx * (xc - (cx - q.x)) + ly * (yc - (cy - q.y)), -q.z), kf - q.z);
-    const T l0 = lc - lx * xc - ly * yc;
-
-    // S[j]: 6 B(c_j), c_j = j - q.z, j = 0 .. KW (registers; levels past K are unused)
+    const RunFrame F = run_frame(src, lx, ly, K, lo_open);
+    // S[j]: 6 B(c_j), c_j = j - q.z, j = 0 .. KW (levels past K are unused)
     T S[KW + 1];
 #pragma unroll
     for (int j = 0; j <= KW; ++j) S[j] = T(0);
-    const int j0 = lo_open ? 0 : 1;
     // the tetrahedron's z range inside the column, and 6 x its volume there
     T colmin = T(1e30), colmax = T(-1e30), msum = T(0);
-
 #pragma unroll 1
     for (int f = 0; f < 4; ++f) {
-        int ia, ib, ic;
-        face_vertices(f, ia, ib, ic);
-        const P3<T> a = sub(src.vtx(ia), q), b = sub(src.vtx(ib), q), c = sub(src.vtx(ic), q);
-        const T mnx = fmin(a.x, fmin(b.x, c.x)), mxx = fmax(a.x, fmax(b.x, c.x));
-        const T mny = fmin(a.y, fmin(b.y, c.y)), mxy = fmax(a.y, fmax(b.y, c.y));
-        if (mxx < xlo || mnx >= xhi || mxy < ylo || mny >= yhi) continue;  // outside the column
-        const P3<T> nf = src.nrm(f);
-        if (nf.z == T(0)) continue;  // vertical face: no projected area
-        const T mnz = fmin(a.z, fmin(b.z, c.z)), mxz = fmax(a.z, fmax(b.z, c.z));
-        const T cmag = fmax(T(1), fmax(fmax(fmax(fabs(mnx), fabs(mxx)), fmax(fabs(mny), fabs(mxy))),
-                                       fmax(fabs(mnz), fabs(mxz))));
-        const T tol = T(8) * roundoff<T>() * cmag;
-        const T ef = dot(nf, a);
-        const T sc = fdiv(ef, dot(nf, nf));
-        const P3<T> o = mk<T>(sc * nf.x, sc * nf.y, sc * nf.z);
-        const T fo = o.z - fmaT(lx, o.x, fmaT(ly, o.y, l0));
-
-        slot_store(E, 0, a, b);
-        slot_store(E, 1, b, c);
-        slot_store(E, 2, c, a);
-        slab_pass<0>(E, xlo, xhi, tol);
-        FaceSums I;
-        yslab_sums(E, ylo, yhi, tol, o, fo, l0, lx, ly, I);
-        colmin = fmin(colmin, I.zmin);
-        colmax = fmax(colmax, I.zmax);
-        msum += I.m6;
-
-        // levels the polygon straddles: jlo .. jhi (c_j - zmin > 0 and zmax - c_j > 0)
-        const T flo = fmin(fmax(floor(I.zmin + q.z) + T(1), T(j0)), kf + T(1));
-        const T fhi = fmin(fmax(ceil(I.zmax + q.z) - T(1), T(-1)), kf);
-        const int jlo = (int)flo, jhi = (int)fhi;
-        // closed forms: below jlo the face is above the level, from jlo on it is (at first
-        // taken as) below it
-#pragma unroll
-        for (int j = 0; j <= KW; ++j) {
-            const T cj = (T)j - q.z;
-            const T v = (j < jlo) ? fmaT(T(3) * cj, I.x2, -I.y6) : I.m6;
-            S[j] += (j >= j0 && j <= K) ? v : T(0);
-        }
-        // straddled levels: subtract the part above the level
-        const T w = fdiv(T(1), fmaT(nf.x, nf.x, nf.y * nf.y));
+        if (!face_meets_column(src, f, F)) continue;
+        FaceRun<KW> R;
+        face_run<KW>(src, f, F, E, R);
 #pragma unroll 1
-        for (int j = jlo; j <= jhi; ++j) {
-            const T cj = (T)j - q.z;
-            const T s = fmaT(-nf.z, cj, ef) * w;
-            const T g = level_fan(E, cj, s * nf.x, s * nf.y);
+        for (int j = R.jlo; j <= R.jhi; ++j) {  // straddled levels: subtract the part above
+            const T cj = (T)j - F.qz;
+            T ox, oy;
+            fan_anchor(R.nx, R.ny, R.nz, R.ef, cj, ox, oy);
+            const T g = level_fan(E, cj, ox, oy);
 #pragma unroll
-            for (int i = 0; i <= KW; ++i) S[i] -= (i == j) ? g : T(0);
+            for (int i = 0; i <= KW; ++i) R.k6[i] -= (i == j) ? g : T(0);
         }
-    }
-    // levels at or below the tetrahedron's lowest point in the column hold exactly 0, and
-    // levels at or above its highest point the column's whole volume: set them so, rather
-    // than leave the rounding of terms that cancel
 #pragma unroll
-    for (int j = 0; j <= KW; ++j) {
-        const T cj = (T)j - q.z;
-        S[j] = (cj <= colmin) ? T(0) : ((cj >= colmax) ? msum : S[j]);
+        for (int j = 0; j <= KW; ++j) S[j] += R.k6[j];
+        colmin = fmin(colmin, R.zmin);
+        colmax = fmax(colmax, R.zmax);
+        msum += R.m6;
     }
-#pragma unroll
-    for (int j = 0; j < KW; ++j) vol[j] = (S[j + 1] - S[j]) * T(1.0 / 6.0);
+    column_finish<KW>(F, S, colmin, colmax, msum, vol);
 }
 
 }  // namespace pse

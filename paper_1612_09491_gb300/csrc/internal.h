@@ -25,7 +25,8 @@ enum StatSlot : int32_t {
 };
 
 struct Workspace {
-    unsigned long long work_counter;   // dynamic work fetching
+    unsigned long long work_counter;   // dynamic work fetching (first pass)
+    unsigned long long work_counter2;  // the same for the guarded pass; the two are reset together
     unsigned long long stats[ST_NUM_U64];
     double mass_in;
     double mass_dropped;

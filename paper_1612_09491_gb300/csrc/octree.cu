@@ -326,9 +326,14 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
 // ---------------------------------------------------------------------------
 // warp-cooperative FP32 path: per sub-batch, rounds of (tetrahedron, leaf) pairs
 // ---------------------------------------------------------------------------
-template <bool STATS, int MINB, Acc A>
+// PASS kPassFp32 visits every (tetrahedron, leaf) pair: it counts the tetrahedra, deposits
+// degenerate ones and those inside one cell of a leaf, and clips the pairs below the guard by
+// column runs.  PASS kPassGuard visits the pairs again and clips only the guarded ones, cell
+// by cell in FP64.
+template <bool STATS, int MINB, Acc A, int PASS>
 __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
 {
+    constexpr bool FIRST = PASS == kPassFp32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
     bind_residuals(P, S);
@@ -340,7 +345,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
 
     for (;;) {
         unsigned long long item = 0;
-        if (lane == 0) item = atomicAdd(&P.ws->work_counter, 1ull);
+        if (lane == 0) item = atomicAdd(FIRST ? &P.ws->work_counter : &P.ws->work_counter2, 1ull);
         item = __shfl_sync(kFull, item, 0);
         if ((int64_t)item >= P.n_items) break;
         int64_t ci = 0, cj = 0, ck = 0;
@@ -372,16 +377,18 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
             if (have) {
                 lattice_tet_raw(P, ci, cj, ck, s, x, k);
                 tet_centroid(P, x, k, cen);
-                if (STATS) {
-            cnt.u[ST_TETS]++;
-            cnt.mass_in += m_t;
-            cnt.u[ST_INVERTED] += ((det6_box(P, x, k) < 0.0) != kuhn_negative(s)) ? 1 : 0;
-        }
-                cnt.add_tgt(P, m_t);
+                if (STATS && FIRST) {
+                    cnt.u[ST_TETS]++;
+                    cnt.mass_in += m_t;
+                    cnt.u[ST_INVERTED] += ((det6_box(P, x, k) < 0.0) != kuhn_negative(s)) ? 1 : 0;
+                }
+                if (FIRST) cnt.add_tgt(P, m_t);
                 if (det6_box(P, x, k) == 0.0) {
-                    add_mass<A>(P, cen, m_t, cnt, STATS);
-                    cnt.add_dep(m_t);
-                    if (STATS) cnt.u[ST_DEGENERATE]++;
+                    if (FIRST) {
+                        add_mass<A>(P, cen, m_t, cnt, STATS);
+                        cnt.add_dep(m_t);
+                        if (STATS) cnt.u[ST_DEGENERATE]++;
+                    }
                 } else {
                     fine_range(P, x, k, f0, f1);
                     live = true;
@@ -399,14 +406,16 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                         to_grid<float>(P, x, k, bc << hit.level, v, base);
                         TetSetup<float> ts;
                         const bool swapped = tet_setup<float>(v, ts);
+                        const bool guard = !(ts.kappa <= P.kappa_max);
 #pragma unroll
                         for (int q = 0; q < 4; ++q) res[q] = mk<float>(0.f, 0.f, 0.f);
-                        if (!(ts.kappa <= P.kappa_max)) {  // rounding residuals for the guarded clip
+                        if (!FIRST && guard) {  // rounding residuals for the guarded clip
                             P3<float> v2[4];
                             int b2[3];
                             to_grid<float>(P, x, k, bc << hit.level, v2, b2, res);
                             if (swapped) swap12(res);
                         }
+                        const bool single = ts.dim[0] == 1 && ts.dim[1] == 1 && ts.dim[2] == 1;
                         if (!tet_ok(base, ts)) {
                             set_error(P.ws, 4, lane);
                             more = false;
@@ -422,7 +431,9 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                 S->org[a][lane] = org;
                             }
                             const int64_t ncell = (int64_t)dim[0] * dim[1] * dim[2];
-                            if (ts.dim[0] == 1 && ts.dim[1] == 1 && ts.dim[2] == 1) {
+                            if (!FIRST && (single || !guard)) {
+                                // the guarded pass: nothing to do for this pair
+                            } else if (single) {
                                 // whole tetrahedron inside one cell of this leaf
                                 cell_add<A>(P, P.out + (int64_t)hit.leaf * bc * bc * bc + (lo[0] - S->org[0][lane]) +
                                               bc * ((lo[1] - S->org[1][lane]) + bc * (lo[2] - S->org[2][lane])),
@@ -431,9 +442,15 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                 if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; }
                             } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(dim)) {
                                 set_error(P.ws, 2, lane);
-                            } else if (ncell > 0) {
-                                npairs = (ts.kappa <= P.kappa_max) ? (int)run_count(dim, ts.axis) : (int)ncell;
+                            } else if (FIRST && guard) {
+                                // left to the guarded pass; counted here
                                 if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
+                            } else if (ncell > 0) {
+                                npairs = FIRST ? (int)run_count(dim, ts.axis) : (int)ncell;
+                                if (STATS && FIRST) {
+                                    cnt.u[ST_BBOX_CELLS] += ncell;
+                                    cnt.u[ST_BIN0 + size_bin(ncell)]++;
+                                }
 #pragma unroll
                                 for (int q = 0; q < 4; ++q) {
                                     S->v[3 * q][lane] = ts.v[q].x;
@@ -453,12 +470,11 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                     S->base[a][lane] = base[a];
                                 }
                                 S->leaf[lane] = hit.leaf;
-                                const int guard = (ts.kappa <= P.kappa_max) ? 0 : 1;
                                 S->rho[lane] = (float)(6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6));
                                 S->lx[lane] = ts.lx;
                                 S->ly[lane] = ts.ly;
                                 S->axis[lane] = ts.axis;
-                                S->guard[lane] = guard;
+                                S->guard[lane] = guard ? 1 : 0;
                                 S->skip[lane] = 0;
                                 {
                                     const int C = ts.axis;
@@ -470,7 +486,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                         }
                     }
                 }
-                coop_pairs<STATS, true, A, true>(P, S, lane, npairs, cnt);
+                coop_pairs<STATS, true, A, PASS>(P, S, lane, npairs, cnt);
                 __syncwarp();
             }
             __syncwarp();
@@ -768,6 +784,34 @@ cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStrea
     return cudaGetLastError();
 }
 
+namespace {
+template <int PASS>
+cudaError_t launch_oct_pass(const DepositParams &p, bool stats, int blocks_per_sm, cudaStream_t st)
+{
+    // blocks_per_sm resident blocks of 128 threads: 2 (255 registers), 3 (170) or 4 (128);
+    // the counting variant (stats) is built for 2 only
+    const int threads = 128;
+    const size_t smem = sizeof(WarpSmem) * (threads / 32);
+    const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
+    const void *k = p.comp ? (stats ? (const void *)k_oct_warp<true, 2, Acc::COMP, PASS>
+                              : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::COMP, PASS>
+                              : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::COMP, PASS>
+                                          : (const void *)k_oct_warp<false, 2, Acc::COMP, PASS>)
+                    : (stats ? (const void *)k_oct_warp<true, 2, Acc::F64, PASS>
+                       : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::F64, PASS>
+                       : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::F64, PASS>
+                                   : (const void *)k_oct_warp<false, 2, Acc::F64, PASS>);
+    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int blocks = persistent_blocks(k, threads, smem);
+    if (blocks > kMaxWarpBlocks) blocks = kMaxWarpBlocks;
+    const int64_t need = (p.n_items + 3) / 4;
+    if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
+    void *args[] = {const_cast<DepositParams *>(&p)};
+    return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
+}
+}  // namespace
+
 cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread_per_tet, bool stats,
                                   int blocks_per_sm, cudaStream_t st)
 {
@@ -782,27 +826,10 @@ cudaError_t launch_octree_deposit(const DepositParams &p, bool fp64, bool thread
         void *args[] = {const_cast<DepositParams *>(&p)};
         return cudaLaunchKernel(k, dim3((unsigned)blocks), dim3(threads), args, 0, st);
     }
-    // blocks_per_sm resident blocks of 128 threads: 2 (255 registers), 3 (170) or 4 (128);
-    // the counting variant (stats) is built for 2 only
-    const int threads = 128;
-    const size_t smem = sizeof(WarpSmem) * (threads / 32);
-    const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
-    const void *k = p.comp ? (stats ? (const void *)k_oct_warp<true, 2, Acc::COMP>
-                              : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::COMP>
-                              : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::COMP>
-                                          : (const void *)k_oct_warp<false, 2, Acc::COMP>)
-                    : (stats ? (const void *)k_oct_warp<true, 2, Acc::F64>
-                       : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::F64>
-                       : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::F64>
-                                   : (const void *)k_oct_warp<false, 2, Acc::F64>);
-    cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the FP32 pass, then the guarded pass over the same pairs
+    cudaError_t err = launch_oct_pass<kPassFp32>(p, stats, blocks_per_sm, st);
     if (err != cudaSuccess) return err;
-    int blocks = persistent_blocks(k, threads, smem);
-    if (blocks > kMaxWarpBlocks) blocks = kMaxWarpBlocks;
-    const int64_t need = (p.n_items + 3) / 4;
-    if (need < blocks) blocks = (int)(need < 1 ? 1 : need);
-    void *args[] = {const_cast<DepositParams *>(&p)};
-    return cudaLaunchKernel(k, dim3(blocks), dim3(threads), args, smem, st);
+    return launch_oct_pass<kPassGuard>(p, stats, blocks_per_sm, st);
 }
 
 }  // namespace pse

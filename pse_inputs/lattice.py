@@ -61,6 +61,11 @@ CONFIGS = {
     3: WorkloadConfig(3, "batching-256c-octree16", 256, -1.5, 4.0, "octree", 256, bc=16, max_level=4),
     4: WorkloadConfig(4, "learned-512c-grid512", 512, -1.5, 4.0, "uniform", 512),
     5: WorkloadConfig(5, "scale-1024c-octree128", 1024, -2.0, 3.0, "octree", 2048, bc=128, max_level=4),
+    # the 1024^3 workload's geometry at 1/64 of its size: 2 finest cells per lattice spacing and
+    # the same spectrum; with P(k) ~ k^-2 the strain variance at a fixed rms displacement (in
+    # spacings) grows as 1/n, so rms 1.5 at 256^3 matches rms 3 at 1024^3.  The case that
+    # profilers capture in full.
+    6: WorkloadConfig(6, "profile-256c-octree32", 256, -2.0, 1.5, "octree", 512, bc=32, max_level=4),
 }
 
 
