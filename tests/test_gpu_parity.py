@@ -552,3 +552,21 @@ def test_inverted_tetrahedra_are_counted_alike_by_every_schedule():
     assert len(counts) == 1 and counts.pop() > 0
     _, st = pse.deposit_uniform(dev(lattice_positions(8)), 8, 16, stats=True)
     assert st["inverted_tets"] == 0
+
+
+def test_slab_partition_sums_to_the_whole_deposit():
+    """Option B's partition on the GPU path: the z-slabs of three ranks, each deposited alone
+    (cube subsets of the whole lattice), sum to the one-shot deposit (each slab renormalised to
+    its own tetrahedra's mass, so the sum keeps the total)."""
+    from paper_1612_09491_gb300 import shard
+    cfg = CONFIGS[1]
+    pos = config_positions(cfg)
+    dpos = dev(pos)
+    whole = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n).cpu().numpy()
+    total = np.zeros_like(whole)
+    for r in range(3):
+        k0, k1 = shard.slab_bounds(cfg.n, 3, r)
+        ids = torch.from_numpy(shard.slab_cube_ids(cfg.n, k0, k1)).cuda()
+        total += pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, cube_ids=ids).cpu().numpy()
+    e = cell_errors(total, whole)
+    assert e["max_rel"] <= 2e-6 and e["mass"] <= MASS32, e
