@@ -56,7 +56,7 @@
 extern "C" {
 #endif
 
-#define PSE_ABI_VERSION 1
+#define PSE_ABI_VERSION 2
 
 #define PSE_OK 0
 #define PSE_ERR_INVALID_ARG -1 /* a null pointer, a bad size or an inconsistent option */
@@ -117,7 +117,11 @@ typedef struct pse_deposit_opts {
                                 sum(m_t) / sum(computed deposits), so total mass is conserved to float64
                                 rounding (every cell moves by the same relative ~1e-8) */
     const int64_t *d_cube_ids; /* NULL: every cube; else deposit only these Lagrangian cubes (device int64
-                                  [n_cube_ids], each in [0, number of cubes); n_cube_ids may be 0) */
+                                  [n_cube_ids], each in [0, number of cubes); n_cube_ids may be 0).
+                                  Accuracy of such subset deposits with the FP32 clip: a cell that
+                                  holds only a sliver of one tetrahedron carries the clip's absolute
+                                  error (about 1e-7 of a whole cell at that tetrahedron's density),
+                                  so relative to its own small mass it is good to about 1e-4 */
     int64_t n_cube_ids;
 } pse_deposit_opts;
 
@@ -135,6 +139,12 @@ typedef struct pse_deposit_stats {
     uint64_t inverted_tets;    /* lattice tetrahedra turned inside out by shell crossing: signed volume of
                                   the other sign than in the Lagrangian lattice (they deposit positive
                                   mass, Sec. 2); explicit tetrahedra: negative signed volume */
+    uint64_t overlapped_cells; /* (tetrahedron, cell) pairs that received a deposit (overlap > 0) */
+    uint64_t column_runs;      /* warp schedules: runs of cells along a tetrahedron's divergence axis that
+                                  one column clip served (the clip work unit; see partial_clips) */
+    double mass_out;           /* mass this call wrote into the output: its in-grid deposits, after the
+                                  renormalisation when that applied (equals mass_in - mass_dropped to
+                                  float64 rounding when it did) */
 } pse_deposit_stats;
 
 /*
@@ -254,8 +264,8 @@ PSE_API void pse_free_octree(pse_octree *oct);
 
 /*
  * The leaf list of pse_build_octree_from_tet_sizes, for callers that cannot allocate
- * memory (code inside CUDA graph capture, plugins whose host owns the device allocator,
- * real-time loops that must not wait on it).  The paper has no counterpart: this is an
+ * memory (plugins whose host application owns the device allocator, real-time loops that
+ * must not wait on it).  The paper has no counterpart: this is an
  * interface variant, not part of the method.  It allocates nothing and does not
  * synchronise: its scratch (work counters and the size histograms) is a fixed 256 KB
  * device array inside the library -- every GPU that loads the library holds it until
@@ -265,8 +275,11 @@ PSE_API void pse_free_octree(pse_octree *oct);
  *   d_n_leaves  device int64 [1]: the number of leaves (may exceed cap: then call again).
  *   max_level   <= 4 (the fixed scratch holds the histograms of levels 0..3); a larger
  *               value returns PSE_ERR_INVALID_ARG without touching the device.
- * The first call on each device resolves the array's device address with that device
- * current; make that first call outside stream capture.  Every call reuses the same
+ * The first call on each device (and the first after a device reset, which creates a new
+ * context and a new copy of the array) resolves the array's device address with that
+ * device current; make that call outside stream capture.  The refinement threshold is
+ * turned into a histogram-bin cutoff on the host exactly as the allocating build turns
+ * it, so thresholds on a bin edge give the same leaves.  Every call reuses the same
  * array (it is cleared at the start of each call): calls that overlap on the GPU, on
  * any stream, race and give wrong results.
  */

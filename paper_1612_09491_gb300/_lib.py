@@ -86,7 +86,8 @@ class DepositStats(ctypes.Structure):
                 ("partial_clips", ctypes.c_uint64), ("fp64_redos", ctypes.c_uint64),
                 ("degenerate_tets", ctypes.c_uint64), ("single_cell_tets", ctypes.c_uint64),
                 ("bin_counts", ctypes.c_uint64 * 8), ("mass_in", ctypes.c_double), ("mass_dropped", ctypes.c_double),
-                ("inverted_tets", ctypes.c_uint64)]
+                ("inverted_tets", ctypes.c_uint64), ("overlapped_cells", ctypes.c_uint64),
+                ("column_runs", ctypes.c_uint64), ("mass_out", ctypes.c_double)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "bin_counts"}

@@ -418,6 +418,13 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
         h_stats->mass_in = hw.mass_in;
         h_stats->mass_dropped = hw.mass_dropped;
         h_stats->inverted_tets = hw.stats[pse::ST_INVERTED];
+        h_stats->overlapped_cells = hw.stats[pse::ST_OVERLAPPED];
+        h_stats->column_runs = hw.stats[pse::ST_RUNS];
+        // the mass this call wrote into the output: its in-grid deposits, times the
+        // renormalisation factor when it applied
+        const double in_grid = hw.mass_deposited - hw.mass_dropped;
+        h_stats->mass_out = (renorm && hw.mass_deposited > 0.0) ? in_grid * (hw.mass_target / hw.mass_deposited)
+                                                                 : in_grid;
         if (hw.error_code != 0)
             return fail(PSE_ERR_DEVICE,
                         hw.error_code == 1 ? "a tetrahedron is wider than the periodic grid (detail %d)"

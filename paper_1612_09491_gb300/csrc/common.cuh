@@ -565,6 +565,7 @@ __device__ __forceinline__ void deposit_clip(const DepositParams &P, const WarpS
 {
     if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
     if (vol > 0.0) {
+        if (STATS) cnt.u[ST_OVERLAPPED]++;
         const double m = (double)(S->rho[t] * (float)vol);
         cnt.add_dep(m);
         if (!deposit_pair<OCT, A>(P, S, t, cx, cy, cz, m) && STATS) cnt.dropped += m;
@@ -613,6 +614,7 @@ __device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, i
         int cx, cy, cz, kw;
         run_cells(S, t, (int)((ent >> 5) & kQMask), (int)((ent >> (5 + kQBits)) & kQMask), w, cx, cy, cz, kw);
         const RecordRun src{S, t, C, (float)cx, (float)cy, (float)cz};
+        if (STATS) cnt.u[ST_RUNS]++;
         float vol[kRun];
         column_volumes<kRun>(src, S->lx[t], S->ly[t], kw, w > 0 || S->cut[t] != 0, vol, &S->poly[0][lane]);
         const float rho = S->rho[t];
@@ -635,6 +637,7 @@ __device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, i
                 else if (cls == CELL_INSIDE) cnt.u[ST_INSIDE_CELLS]++;
             }
             if (j < kw && vol[j] > 0.f) {
+                if (STATS) cnt.u[ST_OVERLAPPED]++;
                 const double m = (double)(rho * vol[j]);
                 cnt.add_dep(m);
                 if (!deposit_pair<OCT, A>(P, S, t, ex, ey, ez, m) && STATS) cnt.dropped += m;
@@ -714,7 +717,7 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                                                       cz + (C == 2 ? j : 0), m) && STATS)
                                 cnt.dropped += m;
                         }
-                        if (STATS) cnt.u[ST_INSIDE_CELLS] += kw;
+                        if (STATS) { cnt.u[ST_INSIDE_CELLS] += kw; cnt.u[ST_OVERLAPPED] += kw; }
                     } else if (cls == CELL_PARTIAL) {
                         ent = q_pack(t, ia, ib, w);
                         partial = true;
@@ -740,7 +743,7 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
                         if (!deposit_pair<OCT, A>(P, S, t, S->lo[0][t] + ix, S->lo[1][t] + iy, S->lo[2][t] + iz, m) &&
                             STATS)
                             cnt.dropped += m;
-                        if (STATS) cnt.u[ST_INSIDE_CELLS]++;
+                        if (STATS) { cnt.u[ST_INSIDE_CELLS]++; cnt.u[ST_OVERLAPPED]++; }
                     } else if (cls == CELL_PARTIAL) {
                         ent = q_pack(t, ix, iy, iz);
                         if (PASS == kPassGuard || (PASS == kPassAll && S->guard[t])) gpartial = true;

@@ -171,14 +171,14 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                         cnt.dropped += m_t;
                     cnt.add_tgt(P, m_t);
                     cnt.add_dep(m_t);
-                    if (STATS) cnt.u[ST_DEGENERATE]++;
+                    if (STATS) { cnt.u[ST_DEGENERATE]++; cnt.u[ST_OVERLAPPED]++; }
                 } else if (ncell == 1) {
                     if (!deposit_cell<A>(P, (int64_t)base[0] + ts.lo[0], (int64_t)base[1] + ts.lo[1],
                                       (int64_t)base[2] + ts.lo[2], m_t) && STATS)
                         cnt.dropped += m_t;
                     cnt.add_tgt(P, m_t);
                     cnt.add_dep(m_t);
-                    if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
+                    if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; cnt.u[ST_OVERLAPPED]++; }
                 } else if (BINNED && split &&
                            (P.model ? ((P.qbits[tid >> 5] >> (tid & 31)) & 1u) != 0
                                     : (ncell > P.split_cells && ncell <= (int64_t)INT32_MAX))) {
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
         }
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P, P.ws);
+    if (P.fixup || STATS) cnt.flush_mass(P, P.ws);
 }
 
 template <bool BINNED, Acc A, int PASS>

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
             centroid_cell(ts.v, c);
             if (!deposit_cell(P, base[0] + c[0], base[1] + c[1], base[2] + c[2], m_t) && STATS) cnt.dropped += m_t;
             cnt.add_dep(m_t);
-            if (STATS) cnt.u[ST_DEGENERATE]++;
+            if (STATS) { cnt.u[ST_DEGENERATE]++; cnt.u[ST_OVERLAPPED]++; }
             continue;
         }
         const int64_t ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
             if (!deposit_cell(P, base[0] + ts.lo[0], base[1] + ts.lo[1], base[2] + ts.lo[2], m_t) && STATS)
                 cnt.dropped += m_t;
             cnt.add_dep(m_t);
-            if (STATS) cnt.u[ST_SINGLE_CELL]++;
+            if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_OVERLAPPED]++; }
             continue;
         }
         // FP32 guard: ill-conditioned tetrahedra are clipped in float64 from their exact vertices
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                         if (STATS) cnt.u[ST_PARTIAL_CLIPS]++;
                     }
                     if (vol > 0.0) {
+                        if (STATS) cnt.u[ST_OVERLAPPED]++;
                         const double m = rho * vol;
                         cnt.add_dep(m);
                         if (!deposit_cell(P, (int64_t)base[0] + cx, (int64_t)base[1] + cy, (int64_t)base[2] + cz, m) &&
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
                 }
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P, P.ws);
+    if (P.fixup || STATS) cnt.flush_mass(P, P.ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
                     cnt.add_dep(m_t);
                     if (STATS) {
                         cnt.u[ts.vol6 == 0.0 ? ST_DEGENERATE : ST_SINGLE_CELL]++;
+                        cnt.u[ST_OVERLAPPED]++;
                         if (ts.vol6 != 0.0) { cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_BIN0]++; }
                     }
                 } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(ts.dim)) {
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(kCoopThreads, 2) k_warp_per_tet(const DepositP
         __syncwarp();
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P, P.ws);
+    if (P.fixup || STATS) cnt.flush_mass(P, P.ws);
 }
 
 // ---------------------------------------------------------------------------

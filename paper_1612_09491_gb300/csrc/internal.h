@@ -20,6 +20,8 @@ enum StatSlot : int32_t {
     ST_DEGENERATE,
     ST_SINGLE_CELL,
     ST_INVERTED,  // tetrahedra whose orientation differs from the Lagrangian one (shell crossing)
+    ST_OVERLAPPED,  // (tetrahedron, cell) pairs that received a deposit
+    ST_RUNS,        // column runs clipped (warp schedules)
     ST_BIN0,  // 8 bins
     ST_NUM_U64 = ST_BIN0 + 8
 };

@@ -1,8 +1,8 @@
 // noalloc.cu -- an octree-build entry point for callers that cannot allocate memory.
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured, plugins inside a host application that owns the device allocator, or
-// real-time loops that must not block on the allocator.  pse_build_octree_leaves_noalloc
+// Some callers cannot call cudaMalloc: plugins inside a host application that owns the
+// device allocator, or real-time loops that must not block on the allocator.
+// pse_build_octree_leaves_noalloc
 // builds the same octree leaf list as pse_build_octree_from_tet_sizes, but it
 // allocates nothing: its scratch (the work counters and the per-level size
 // histograms) lives in a file-scope device array of kScratchBytes, and the leaf
@@ -30,6 +30,36 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
+void *g_ctx[kMaxDevices] = {};  // the context the cached address belongs to
+
+// The current driver context (nullptr if it cannot be read): a device reset creates a new
+// one, and with it a new copy of g_scratch at another address.
+void *current_context()
+{
+    using GetCurrent = int (*)(void **);
+    static GetCurrent fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<GetCurrent>(f);
+    });
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
+
+// The first histogram bin whose lower edge 10^(-3 + 6 b / 64) cells is not below the
+// threshold, computed on the host exactly as the allocating build computes the edges: a
+// node is refined when its lower-median bin lies below this cutoff.
+int refine_cutoff(double threshold)
+{
+    int b = 0;
+    while (b < 64 && std::pow(10.0, -3.0 + 6.0 * b / 64.0) < threshold) ++b;
+    return b;
+}
 
 
 size_t hist_bytes_of(int max_level)
@@ -42,7 +72,7 @@ size_t hist_bytes_of(int max_level)
 // Depth-first traversal of the refinement decisions (lower-median bin edge below the
 // threshold), writing leaves (level, ix, iy, iz) into out; *count receives the number
 // of leaves even when it exceeds cap.  One thread: the tree has at most 8^4 leaves.
-__global__ void k_octree_decide(const unsigned *__restrict__ hist, int max_level, double threshold,
+__global__ void k_octree_decide(const unsigned *__restrict__ hist, int max_level, int cutoff,
                                 int32_t *__restrict__ out, long long cap, long long *__restrict__ count)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -69,7 +99,7 @@ __global__ void k_octree_decide(const unsigned *__restrict__ hist, int max_level
                         cum += h[b];
                         if (cum > k) { bin = b; break; }
                     }
-                    refine = pow(10.0, -3.0 + 6.0 * bin / 64.0) < threshold;
+                    refine = bin < cutoff;
                 }
             }
             if (!refine) {
@@ -141,11 +171,13 @@ int pse_build_octree_leaves_noalloc(const float *d_pos, const pse_lattice *lat, 
     {
         // set-up, once per device, with that device current
         std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
+        void *ctx = current_context();
+        if (!g_addr[dev] || ctx != g_ctx[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_scratch);
             if (e != cudaSuccess) return fail(PSE_ERR_CUDA, cudaGetErrorString(e));
             g_addr[dev] = p;
+            g_ctx[dev] = ctx;
         }
         base = g_addr[dev];
     }
@@ -173,7 +205,7 @@ int pse_build_octree_leaves_noalloc(const float *d_pos, const pse_lattice *lat, 
         e = pse::launch_octree_hist(p, hist, st);
         if (e != cudaSuccess) return fail(PSE_ERR_CUDA, cudaGetErrorString(e));
     }
-    k_octree_decide<<<1, 32, 0, st>>>(hist, max_level, edge_threshold_cells, d_leaves, (long long)cap,
+    k_octree_decide<<<1, 32, 0, st>>>(hist, max_level, refine_cutoff(edge_threshold_cells), d_leaves, (long long)cap,
                                       reinterpret_cast<long long *>(d_n_leaves));
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PSE_ERR_CUDA, cudaGetErrorString(e));

@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
         if (det6_box(P, x, k) == 0.0) {
             add_mass(P, cen, m_t, cnt, STATS);
             cnt.add_dep(m_t);
-            if (STATS) cnt.u[ST_DEGENERATE]++;
+            if (STATS) { cnt.u[ST_DEGENERATE]++; cnt.u[ST_OVERLAPPED]++; }
             continue;
         }
         int64_t f0[3], f1[3];
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
                         double vol = 0.0;
                         if (single) {
                             vol = ts.vol6 / 6.0;
-                            if (STATS) cnt.u[ST_SINGLE_CELL]++;
+                            if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_OVERLAPPED]++; }
                         } else {
                             const int cls = classify_cell<T>(ts.n, ts.e, ts.pos, ts.neg, (T)cx, (T)cy, (T)cz);
                             if (cls == CELL_INSIDE) {
@@ -312,6 +312,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
                             }
                         }
                         if (vol > 0.0) {
+                            if (STATS) cnt.u[ST_OVERLAPPED]++;
                             const double m = rho * vol;
                             cnt.add_dep(m);
                             cell_add(P, blk + (cx - org[0]) + bc * ((cy - org[1]) + bc * (cz - org[2])), m);
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
         }
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P, P.ws);
+    if (P.fixup || STATS) cnt.flush_mass(P, P.ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -387,7 +388,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                     if (FIRST) {
                         add_mass<A>(P, cen, m_t, cnt, STATS);
                         cnt.add_dep(m_t);
-                        if (STATS) cnt.u[ST_DEGENERATE]++;
+                        if (STATS) { cnt.u[ST_DEGENERATE]++; cnt.u[ST_OVERLAPPED]++; }
                     }
                 } else {
                     fine_range(P, x, k, f0, f1);
@@ -439,7 +440,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                               bc * ((lo[1] - S->org[1][lane]) + bc * (lo[2] - S->org[2][lane])),
                                           m_t);
                                 cnt.add_dep(m_t);
-                                if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; }
+                                if (STATS) { cnt.u[ST_SINGLE_CELL]++; cnt.u[ST_BBOX_CELLS]++; cnt.u[ST_OVERLAPPED]++; }
                             } else if (ncell > (int64_t)(1 << 25) || !dims_fit_queue(dim)) {
                                 set_error(P.ws, 2, lane);
                             } else if (FIRST && guard) {
@@ -493,7 +494,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
         }
     }
     if (STATS) cnt.flush(P.ws);
-    if (P.fixup) cnt.flush_mass(P, P.ws);
+    if (P.fixup || STATS) cnt.flush_mass(P, P.ws);
 }
 
 // ---------------------------------------------------------------------------

@@ -80,8 +80,9 @@ int main(void) {
          offsetof(pse_lattice, periodic), offsetof(pse_lattice, box));
   printf("%zu %zu %zu %zu\n", sizeof(pse_deposit_opts), offsetof(pse_deposit_opts, guard_eps),
          offsetof(pse_deposit_opts, d_cube_ids), offsetof(pse_deposit_opts, n_cube_ids));
-  printf("%zu %zu %zu\n", sizeof(pse_deposit_stats), offsetof(pse_deposit_stats, bin_counts),
-         offsetof(pse_deposit_stats, mass_dropped));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(pse_deposit_stats), offsetof(pse_deposit_stats, bin_counts),
+         offsetof(pse_deposit_stats, mass_dropped), offsetof(pse_deposit_stats, overlapped_cells),
+         offsetof(pse_deposit_stats, mass_out));
   printf("%zu %zu %zu %zu\n", sizeof(pse_tuning), offsetof(pse_tuning, split_cells),
          offsetof(pse_tuning, chunk_cells), offsetof(pse_tuning, use_graph));
   return 0;
@@ -94,13 +95,14 @@ int main(void) {
     La, O, S = _lib.Lattice, _lib.DepositOpts, _lib.DepositStats
     assert got[0] == [ctypes.sizeof(La), La.particle_mass.offset, La.periodic.offset, La.box.offset]
     assert got[1] == [ctypes.sizeof(O), O.guard_eps.offset, O.d_cube_ids.offset, O.n_cube_ids.offset]
-    assert got[2] == [ctypes.sizeof(S), S.bin_counts.offset, S.mass_dropped.offset]
+    assert got[2] == [ctypes.sizeof(S), S.bin_counts.offset, S.mass_dropped.offset, S.overlapped_cells.offset,
+                      S.mass_out.offset]
     Tu = _lib.Tuning
     assert got[3] == [ctypes.sizeof(Tu), Tu.split_cells.offset, Tu.chunk_cells.offset, Tu.use_graph.offset]
 
 
 def test_abi_version(L):
-    assert L.pse_abi_version() == 1
+    assert L.pse_abi_version() == 2
 
 
 def test_invalid_arguments_return_codes(L):

@@ -517,6 +517,15 @@ def test_compensated_accumulation_in_the_baseline_kernels(sched):
     got = pse.deposit_uniform(dev(pos), n, g, precision=pse.PSE_FP32_COMPENSATED, schedule=sched).cpu().numpy()
     e = cell_errors(got, ref)
     assert e["max_rel"] <= TOL32 and e["mass"] <= MASS32, e
+    # without the renormalisation (which forces the total mass by construction), the (hi, lo)
+    # pairs must carry the same sums as FP64 reductions of the same FP32 clips: a lost lo word
+    # would move cells by ~1e-7
+    raw_c = pse.deposit_uniform(dev(pos), n, g, precision=pse.PSE_FP32_COMPENSATED, schedule=sched,
+                                mass_fixup=False).cpu().numpy()
+    raw_f = pse.deposit_uniform(dev(pos), n, g, precision=pse.PSE_FP32_FP64ACC, schedule=sched,
+                                mass_fixup=False).cpu().numpy()
+    e = cell_errors(raw_c, raw_f)
+    assert e["max_rel"] <= 1e-9 and abs(raw_c.sum() - raw_f.sum()) <= 1e-12, e
     if sched == pse.PSE_THREAD_PER_TET:
         dpos = dev(pos)
         oct_ = pse.build_octree_from_tet_sizes(dpos, n, 4, 3, 2.0)
@@ -570,3 +579,21 @@ def test_slab_partition_sums_to_the_whole_deposit():
         total += pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, cube_ids=ids).cpu().numpy()
     e = cell_errors(total, whole)
     assert e["max_rel"] <= 2e-6 and e["mass"] <= MASS32, e
+
+
+def test_stats_overlapped_cells_and_mass_out():
+    """The counters added to pse_deposit_stats: every deposit lands in a cell counted as
+    overlapped (at least one per tetrahedron, at most its partial plus inside cells), the
+    column runs of the warp schedule serve its partial cells (each run at most 2 cells), and
+    mass_out is the mass written into the grid."""
+    cfg = CONFIGS[1]
+    dpos = dev(config_positions(cfg))
+    for prec, sched in ((pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE), (pse.PSE_FP64_PLAIN, pse.PSE_THREAD_PER_TET)):
+        m, st = pse.deposit_uniform(dpos, cfg.n, cfg.grid_n, precision=prec, schedule=sched, stats=True)
+        assert st["tets"] <= st["overlapped_cells"] <= st["partial_clips"] + st["inside_cells"] + st["tets"]
+        assert abs(st["mass_out"] - float(m.sum())) <= 1e-13
+        assert abs(st["mass_out"] - 1.0) <= 1e-12
+        if sched == pse.PSE_WARP_COOPERATIVE:
+            assert 0 < st["column_runs"] and st["partial_clips"] - st["fp64_redos"] <= 2 * st["column_runs"]
+        else:
+            assert st["column_runs"] == 0

@@ -1,8 +1,8 @@
 """The allocation-free octree build (pse_build_octree_leaves_noalloc).
 
-Callers that cannot allocate device memory -- code running inside CUDA graph
-capture, plugins whose host application owns the device allocator, real-time loops
-that must not wait on the allocator -- use this entry point: its scratch is a fixed
+Callers that cannot allocate device memory -- plugins whose host application owns the
+device allocator, real-time loops that must not wait on the allocator -- use this entry
+point: its scratch is a fixed
 file-scope device array and the leaf list goes into a buffer the caller owns.  It
 must give exactly the leaves of pse_build_octree_from_tet_sizes, call after call
 (the scratch keeps the previous call's contents, so it has to be cleared every time),
@@ -34,18 +34,20 @@ def squeezed_lattice(n, center, factor=0.3, radius=0.22, seed=0):
     return np.mod(p, 1.0).astype(np.float32)
 
 
-def noalloc_leaves(L, pos, n, bc, max_level, cap=8 ** 4):
+def noalloc_leaves(L, pos, n, bc, max_level, cap=8 ** 4, threshold=2.0, whole=True):
     dpos = torch.from_numpy(pos).cuda()
     lat = pse.lattice(n)
     d_leaves = torch.full((cap, 4), -1, dtype=torch.int32, device="cuda")
     d_n = torch.full((1,), -1, dtype=torch.int64, device="cuda")
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = L.pse_build_octree_leaves_noalloc(ctypes.c_void_p(dpos.data_ptr()), ctypes.byref(lat), bc, max_level,
-                                           2.0, ctypes.c_void_p(d_leaves.data_ptr()), cap,
+                                           float(threshold), ctypes.c_void_p(d_leaves.data_ptr()), cap,
                                            ctypes.c_void_p(d_n.data_ptr()), stream)
     assert rc == _lib.PSE_OK, L.pse_last_error().decode()
     torch.cuda.synchronize()
     count = int(d_n.item())
+    if not whole:
+        return count, d_leaves.cpu().numpy()
     assert 0 < count <= cap
     return d_leaves[:count].cpu().numpy()
 
@@ -77,3 +79,28 @@ def test_noalloc_build_rejects_trees_beyond_its_scratch(L):
                                            ctypes.c_void_p(d_n.data_ptr()), None)
     assert rc == _lib.PSE_ERR_INVALID_ARG
     assert "scratch" in L.pse_last_error().decode()
+
+
+def test_noalloc_build_thresholds_on_bin_edges(L):
+    """A threshold equal to a histogram bin's lower edge: the cutoff is taken on the host the
+    way the allocating build compares edges, so both give the same leaves."""
+    n, bc, ml = 16, 4, 4
+    pos = squeezed_lattice(n, (0.4, 0.4, 0.6), seed=7)
+    for b in (28, 30, 33, 36):
+        thr = 10.0 ** (-3.0 + 6.0 * b / 64.0)
+        got = noalloc_leaves(L, pos, n, bc, ml, threshold=thr)
+        exp = pse.build_octree_from_tet_sizes(torch.from_numpy(pos).cuda(), n, bc, ml, thr).leaves()
+        np.testing.assert_array_equal(got, exp)
+
+
+def test_noalloc_build_truncates_at_cap_and_builds_one_level(L):
+    n, bc, ml = 16, 4, 4
+    pos = squeezed_lattice(n, (0.3, 0.6, 0.4), seed=1)
+    exp = pse.build_octree_from_tet_sizes(torch.from_numpy(pos).cuda(), n, bc, ml, 2.0).leaves()
+    assert len(exp) > 8
+    cap = len(exp) // 2
+    count, buf = noalloc_leaves(L, pos, n, bc, ml, cap=cap, whole=False)
+    assert count == len(exp)                       # the full count, so the caller can retry
+    np.testing.assert_array_equal(buf, exp[:cap])  # and the first cap leaves
+    root = noalloc_leaves(L, pos, n, bc, 0)        # max_level 0: the root alone
+    np.testing.assert_array_equal(root, [[0, 0, 0, 0]])
