@@ -276,6 +276,7 @@ struct Counters {
     double tgt;            // explicit tetrahedra: sum of m_t
     unsigned ntgt;         // lattice tetrahedra (each P.m_tet)
     double dep, dep_c;     // Kahan sum of deposits and its compensation
+    double dep_b;          // plain sum of the deposits since the last fold (a few dozen)
     __device__ void zero()
     {
 #pragma unroll
@@ -289,21 +290,27 @@ struct Counters {
         ntgt = 0;
         dep = 0.0;
         dep_c = 0.0;
+        dep_b = 0.0;
     }
     __device__ __forceinline__ void add_tgt(const DepositParams &P, double m_t)
     {
         if (P.src == SRC_TETS) tgt += m_t;
         else ++ntgt;
     }
-    __device__ __forceinline__ void add_dep(double m)
+    __device__ __forceinline__ void add_dep(double m) { dep_b += m; }
+    // fold the batch into the Kahan sum (after every round of pairs, every tetrahedron of
+    // the thread kernels, and before the flush)
+    __device__ __forceinline__ void fold_dep()
     {
-        const double y = m - dep_c;
+        const double y = dep_b - dep_c;
         const double t = dep + y;
         dep_c = (t - dep) - y;
         dep = t;
+        dep_b = 0.0;
     }
     __device__ void flush_mass(const DepositParams &P, Workspace *ws)
     {
+        fold_dep();
         double a = fma((double)ntgt, P.m_tet, tgt), b = dep - dep_c;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -439,7 +446,8 @@ __device__ __forceinline__ void store_record(WarpSmem *S, int lane, const TetSet
         S->base[a][lane] = base[a];
     }
     const int guard = (ts.kappa <= kappa_max) ? 0 : 1;
-    S->rho[lane] = (float)(6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6));
+    S->rho[lane] = guard ? (float)(6.0 * m_t / exact_vol6(ts.v, res, ts.vol6))
+                         : __fdiv_rn((float)(6.0 * m_t), (float)ts.vol6);
     S->lx[lane] = ts.lx;
     S->ly[lane] = ts.ly;
     S->axis[lane] = ts.axis;
@@ -785,6 +793,7 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
         }
         if (last && qn == 0 && gn == 0) break;
     }
+    cnt.fold_dep();
 }
 
 

@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(128) k_thread_per_tet(const DepositParams P)
     const int64_t n_tets = (P.src == SRC_TETS) ? P.n_units : 6 * P.n_units;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
          t += (int64_t)gridDim.x * blockDim.x) {
+        cnt.fold_dep();  // the previous tetrahedron's deposits
         P3<T> v[4];
         P3<float> res[4];
         int base[3];

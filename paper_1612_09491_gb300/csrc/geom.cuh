@@ -160,7 +160,7 @@ PSE_HD P3<T> pick4(const P3<T> (&p)[4], int i)
 
 // ---------------------------------------------------------------------------
 // Polygon clipping on an edge list (slots of directed edges a -> b; the polygon
-// stays a closed chain; dropped edges collapse onto the local origin).  A slab pass
+// stays a closed chain; a dropped edge collapses to a point and keeps zero length).  A slab pass
 // clips against the two parallel planes lo <= c < hi of one axis at once and appends
 // the two edges it creates on them (exit -> entry).  Classification uses a rounding
 // tolerance: a coordinate within tol of a plane counts as lying on it (on lo: inside;
@@ -172,6 +172,19 @@ PSE_HD T coord(const P3<T> &p, int ax)
 {
     return ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
 }
+
+// t clamped to [0, 1] (NaN -> 0): an edge's crossing point stays on the edge, finite even for
+// edges parallel to the plane, so an edge that a pass drops can be kept as a zero-length edge
+// at that point (it adds exactly nothing to any sum) instead of being moved elsewhere.
+PSE_HD float sat01(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __saturatef(x);
+#else
+    return x > 0.f ? (x < 1.f ? x : 1.f) : 0.f;
+#endif
+}
+PSE_HD double sat01(double x) { return x > 0.0 ? (x < 1.0 ? x : 1.0) : 0.0; }
 
 // point of edge a -> b at parameter t, with coordinate `ax` set exactly to s
 template <class T>
@@ -197,13 +210,11 @@ PSE_HD void clip_slab(P3<T> (&A)[7], P3<T> (&B)[7], int ax, T lo, T hi, T tol)
         const bool a_lo = ca < lo - tol, b_lo = cb < lo - tol;   // below the slab
         const bool a_hi = ca >= hi - tol, b_hi = cb >= hi - tol; // above the slab (on hi counts as above)
         const T inv = fdiv(T(1), cb - ca);
-        const P3<T> pl = at_plane(a, b, (lo - ca) * inv, ax, lo);
-        const P3<T> ph = at_plane(a, b, (hi - ca) * inv, ax, hi);
-        const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
-        P3<T> na = a_lo ? pl : (a_hi ? ph : a);
-        P3<T> nb = b_lo ? pl : (b_hi ? ph : b);
-        na = drop ? z0 : na;
-        nb = drop ? z0 : nb;
+        const P3<T> pl = at_plane(a, b, sat01((lo - ca) * inv), ax, lo);
+        const P3<T> ph = at_plane(a, b, sat01((hi - ca) * inv), ax, hi);
+        // an edge wholly outside becomes the zero-length edge (pl, pl) or (ph, ph)
+        const P3<T> na = a_lo ? pl : (a_hi ? ph : a);
+        const P3<T> nb = b_lo ? pl : (b_hi ? ph : b);
         A[k] = na;
         B[k] = nb;
         xl = (!a_lo && b_lo) ? pl : xl;
@@ -253,18 +264,17 @@ PSE_HD T split_zslab(const P3<T> (&A)[7], const P3<T> (&B)[7], T lo, T hi, T tol
         const bool a_lo = a.z < lo - tol, b_lo = b.z < lo - tol;
         const bool a_hi = a.z >= hi - tol, b_hi = b.z >= hi - tol;
         const T inv = fdiv(T(1), b.z - a.z);
-        const P3<T> pl = at_plane(a, b, (lo - a.z) * inv, 2, lo);
-        const P3<T> ph = at_plane(a, b, (hi - a.z) * inv, 2, hi);
+        const P3<T> pl = at_plane(a, b, sat01((lo - a.z) * inv), 2, lo);
+        const P3<T> ph = at_plane(a, b, sat01((hi - a.z) * inv), 2, hi);
         // the part below lo: whole edge, or from an endpoint to pl
         const P3<T> ba = a_lo ? a : pl, bb = b_lo ? b : pl;
         below += (a_lo || b_lo) ? fan_const(ba, bb, lo, l0, lx, ly) : T(0);
         const P3<T> ua = a_hi ? a : ph, ub = b_hi ? b : ph;
         above += (a_hi || b_hi) ? fan_const(ua, ub, hi, l0, lx, ly) : T(0);
-        // the part in between
-        const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
+        // the part in between (an edge wholly below or above is zero-length here and adds 0)
         const P3<T> na = a_lo ? pl : (a_hi ? ph : a);
         const P3<T> nb = b_lo ? pl : (b_hi ? ph : b);
-        mid += drop ? T(0) : fan_mid(na, nb, o, fo, l0, lx, ly);
+        mid += fan_mid(na, nb, o, fo, l0, lx, ly);
         xl = (!a_lo && b_lo) ? pl : xl;
         nl = (a_lo && !b_lo) ? pl : nl;
         xh = (!a_hi && b_hi) ? ph : xh;
@@ -526,8 +536,13 @@ PSE_HD bool tet_setup(P3<T> (&v)[4], TetSetup<T> &s)
         for (int f = 0; f < 4; ++f) na[f] = to_axis(s.n[f], s.axis);
         ref_slopes<T>(na, s.lx, s.ly);
     }
-    const double denom = s.vol6 > 0.0 ? s.vol6 : 1e-300;
-    s.kappa = (float)((double)area2 * sqrt((double)lmax2) / denom);
+    if constexpr (sizeof(T) == 4) {
+        // a threshold test only: float is enough (a volume below float's range gives inf: guarded)
+        s.kappa = area2 * sqrtf(lmax2) / (float)s.vol6;
+    } else {
+        const double denom = s.vol6 > 0.0 ? s.vol6 : 1e-300;
+        s.kappa = (float)((double)area2 * sqrt((double)lmax2) / denom);
+    }
     return d6 < 0.0;
 }
 
@@ -592,13 +607,10 @@ PSE_HD void slab_pass(float2 *E, float lo, float hi, float tol)
         const bool a_lo = ca < lo - tol, b_lo = cb < lo - tol;
         const bool a_hi = ca >= hi - tol, b_hi = cb >= hi - tol;
         const T inv = fdiv(T(1), cb - ca);
-        const P3<T> pa = at_plane(ea, eb, (lo - ca) * inv, AX, lo);
-        const P3<T> ph = at_plane(ea, eb, (hi - ca) * inv, AX, hi);
-        const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
-        P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
-        P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
-        na = drop ? z0 : na;
-        nb = drop ? z0 : nb;
+        const P3<T> pa = at_plane(ea, eb, sat01((lo - ca) * inv), AX, lo);
+        const P3<T> ph = at_plane(ea, eb, sat01((hi - ca) * inv), AX, hi);
+        const P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
+        const P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
         slot_store(E, k, na, nb);
         xl = (!a_lo && b_lo) ? pa : xl;
         nl = (a_lo && !b_lo) ? pa : nl;
@@ -664,16 +676,15 @@ PSE_HD float overlap_volume_rolled(const P3<float> (&p)[4], const P3<float> (&n)
                 const bool a_lo = ea.z < zlo - tol, b_lo = eb.z < zlo - tol;
                 const bool a_hi = ea.z >= zhi - tol, b_hi = eb.z >= zhi - tol;
                 const T inv = fdiv(T(1), eb.z - ea.z);
-                const P3<T> pa = at_plane(ea, eb, (zlo - ea.z) * inv, 2, zlo);
-                const P3<T> ph = at_plane(ea, eb, (zhi - ea.z) * inv, 2, zhi);
+                const P3<T> pa = at_plane(ea, eb, sat01((zlo - ea.z) * inv), 2, zlo);
+                const P3<T> ph = at_plane(ea, eb, sat01((zhi - ea.z) * inv), 2, zhi);
                 const P3<T> ba = a_lo ? ea : pa, bb = b_lo ? eb : pa;
                 below += (a_lo || b_lo) ? fan_const(ba, bb, zlo, l0, lx, ly) : T(0);
                 const P3<T> ua = a_hi ? ea : ph, ub = b_hi ? eb : ph;
                 above += (a_hi || b_hi) ? fan_const(ua, ub, zhi, l0, lx, ly) : T(0);
-                const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
                 const P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
                 const P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
-                mid += drop ? T(0) : fan_mid(na, nb, o, fo, l0, lx, ly);
+                mid += fan_mid(na, nb, o, fo, l0, lx, ly);
                 xl = (!a_lo && b_lo) ? pa : xl;
                 nl = (a_lo && !b_lo) ? pa : nl;
                 xh = (!a_hi && b_hi) ? ph : xh;
@@ -739,25 +750,21 @@ PSE_HD void yslab_sums(float2 *E, float lo, float hi, float tol, const P3<float>
         const bool a_lo = ea.y < lo - tol, b_lo = eb.y < lo - tol;
         const bool a_hi = ea.y >= hi - tol, b_hi = eb.y >= hi - tol;
         const T inv = fdiv(T(1), eb.y - ea.y);
-        const P3<T> pa = at_plane(ea, eb, (lo - ea.y) * inv, 1, lo);
-        const P3<T> ph = at_plane(ea, eb, (hi - ea.y) * inv, 1, hi);
-        const bool drop = (a_lo && b_lo) || (a_hi && b_hi);
-        P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
-        P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
-        na = drop ? z0 : na;
-        nb = drop ? z0 : nb;
+        const P3<T> pa = at_plane(ea, eb, sat01((lo - ea.y) * inv), 1, lo);
+        const P3<T> ph = at_plane(ea, eb, sat01((hi - ea.y) * inv), 1, hi);
+        const P3<T> na = a_lo ? pa : (a_hi ? ph : ea);
+        const P3<T> nb = b_lo ? pa : (b_hi ? ph : eb);
         slot_store(E, k, na, nb);
         xl = (!a_lo && b_lo) ? pa : xl;
         nl = (a_lo && !b_lo) ? pa : nl;
         xh = (!a_hi && b_hi) ? ph : xh;
         nh = (a_hi && !b_hi) ? ph : nh;
-        // a dropped edge is (0, 0): it adds nothing to the sums
+        // a dropped edge has zero length: it adds nothing to the sums
         const T cr = cross_xy(na, nb);
         m6 += fan_mid(na, nb, o, fo, l0, lx, ly);
         x2 += cr;
         y6 += cr * fmaT(T(3), l0, fmaT(lx, na.x + nb.x, ly * (na.y + nb.y)));
-        // z range over edges of nonzero length (edges the x pass dropped are (0, 0) and
-        // carry no vertex of the polygon)
+        // z range over edges of nonzero length (dropped edges carry no vertex of the polygon)
         const bool live = na.x != nb.x || na.y != nb.y || na.z != nb.z;
         zmn = live ? fmin(zmn, fmin(na.z, nb.z)) : zmn;
         zmx = live ? fmax(zmx, fmax(na.z, nb.z)) : zmx;

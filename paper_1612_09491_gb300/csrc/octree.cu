@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
     const int64_t bc = P.bc;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_tets;
          t += (int64_t)gridDim.x * blockDim.x) {
+        cnt.fold_dep();  // the previous tetrahedron's deposits
         int64_t ci, cj, ck;
         if (!cube_of_unit(P, t / 6, ci, cj, ck)) {
             set_error(P.ws, 3, (int)((t / 6) & 0x7fffffff));
@@ -377,7 +378,6 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
             int64_t f0[3] = {0, 0, 0}, f1[3] = {-1, -1, -1}, cursor = 0;
             if (have) {
                 lattice_tet_raw(P, ci, cj, ck, s, x, k);
-                tet_centroid(P, x, k, cen);
                 if (STATS && FIRST) {
                     cnt.u[ST_TETS]++;
                     cnt.mass_in += m_t;
@@ -386,6 +386,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                 if (FIRST) cnt.add_tgt(P, m_t);
                 if (det6_box(P, x, k) == 0.0) {
                     if (FIRST) {
+                        tet_centroid(P, x, k, cen);
                         add_mass<A>(P, cen, m_t, cnt, STATS);
                         cnt.add_dep(m_t);
                         if (STATS) { cnt.u[ST_DEGENERATE]++; cnt.u[ST_OVERLAPPED]++; }
@@ -471,7 +472,8 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                     S->base[a][lane] = base[a];
                                 }
                                 S->leaf[lane] = hit.leaf;
-                                S->rho[lane] = (float)(6.0 * m_t / (guard ? exact_vol6(ts.v, res, ts.vol6) : ts.vol6));
+                                S->rho[lane] = guard ? (float)(6.0 * m_t / exact_vol6(ts.v, res, ts.vol6))
+                                                     : __fdiv_rn((float)(6.0 * m_t), (float)ts.vol6);
                                 S->lx[lane] = ts.lx;
                                 S->ly[lane] = ts.ly;
                                 S->axis[lane] = ts.axis;
