@@ -47,17 +47,20 @@ SLAB = 64                    # z-slab of the streamed calls, cube layers
 THRESHOLD_CELLS = 2.0        # octree refinement: median mean edge below 2 cells
 TUNING = {"blocks_per_sm": 4}
 
-# Algorithmic work per unit for the ALU roofline (FP32 floating-point operations, FMA = 2):
-# per tetrahedron the determinant, bounding box and face planes; per bounding-box cell one
-# classification against 4 planes; per partial cell the share of its column clip.  The
-# figures are counted by tests/test_flop_model_host.py on the workloads' own tetrahedra.
-FLOP_PER_TET = 150.0
-FLOP_PER_BBOX_CELL = 32.0
-FLOP_PER_CLIP = 620.0
+# Algorithmic work per unit for the ALU roofline (floating-point operations, FMA = 2; min,
+# max, compares and floor are not counted): per tetrahedron the set-up (determinant, bounding
+# box, face planes, divergence axis, reference plane, conditioning); per bounding-box cell one
+# classification against the 4 face planes; per clipped run (up to 2 cells of one column) the
+# column clip.  tests/test_flop_model_host.py counts these on Zel'dovich tetrahedra of the
+# deposit workloads' spectrum at three cell scales, with the kernels' own templates, and
+# checks these figures against the counts.
+FLOP_PER_TET = 222.0
+FLOP_PER_BBOX_CELL = 29.0
+FLOP_PER_RUN = 2000.0
 SM_COUNT_GB300 = 152
 SM_MAX_MHZ_GB300 = 2070.0  # the part's maximum SM clock
 FP32_LANES_PER_SM = 128
-PRECISION = "fp32 clip, fp64 redo of guarded tetrahedra, fp64 accumulation, mass fix-up"
+PRECISION = "fp32 clip, fp64 clip of guarded tetrahedra (exact vertices), fp64 accumulation, mass fix-up"
 PROFILES = os.path.join(ROOT, "profiles")
 
 
@@ -186,7 +189,7 @@ def roofline_alu(st, kernel_ms, sms, peaks, prof, units_key, units):
     kernel's measured duration, against 152 SMs x 128 lanes x 2 FLOP x max clock.  DRAM traffic
     and issued instructions come from the committed ncu summary when it was taken on these
     very sources (else null)."""
-    alg = FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] + FLOP_PER_CLIP * st["partial_clips"]
+    alg = FLOP_PER_TET * st["tets"] + FLOP_PER_BBOX_CELL * st["bbox_cells"] + FLOP_PER_RUN * st["column_runs"]
     peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ_GB300 * 1e6 / 1e12
     achieved = alg / (kernel_ms * 1e-3) / 1e12
     fresh = prof.get("source_digest") == source_digest()
@@ -209,8 +212,8 @@ def roofline_alu(st, kernel_ms, sms, peaks, prof, units_key, units):
             "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 FLOP x "
                            f"{SM_MAX_MHZ_GB300:.0f} MHz (of measured: FMA microbenchmark beside it)",
             "measured_fma_tflops": peaks["fp32_tflops"] if peaks else None,
-            "flop_model": {"per_tet": FLOP_PER_TET, "per_bbox_cell": FLOP_PER_BBOX_CELL, "per_partial_clip":
-                           FLOP_PER_CLIP}}, issue
+            "flop_model": {"per_tet": FLOP_PER_TET, "per_bbox_cell": FLOP_PER_BBOX_CELL, "per_clipped_run":
+                           FLOP_PER_RUN}}, issue
 
 
 # ------------------------------------------------------------ oracle legs ----
@@ -259,25 +262,133 @@ def oracle_blocks(blocks, m, n, seconds):
                       f"deposited alone at the workload's finest cell size, {t_tot:.1f} s"}, grids
 
 
+KUHN_PERMS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def lattice_tets_cells(pos, dims, cubes, scale, periodic):
+    """float64 vertices [T, 4, 3] in cells (positions x scale) of the Kuhn tetrahedra of the
+    given cubes (int64 tensor of cube ids, x fastest) of a lattice of dims particles: corners
+    000, e_a, e_a + e_b, 111 for the six axis orders, each corner moved to the periodic image
+    nearest corner 000 when `periodic`."""
+    import torch
+    n0, n1, n2 = dims
+    c0, c1 = (n0, n1) if periodic else (n0 - 1, n1 - 1)
+    i, j, k = cubes % c0, (cubes // c0) % c1, cubes // (c0 * c1)
+
+    def corner(di, dj, dk):
+        ii, jj, kk = i + di, j + dj, k + dk
+        if periodic:
+            ii, jj, kk = ii % n0, jj % n1, kk % n2
+        return pos[ii + n0 * (jj + n1 * kk)].double()
+
+    p0 = corner(0, 0, 0)
+    unit = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+    out = []
+    for a, b, _ in KUHN_PERMS:
+        ea = unit[a]
+        eab = tuple(x + y for x, y in zip(unit[a], unit[b]))
+        vs = [p0]
+        for off in (ea, eab, (1, 1, 1)):
+            d = corner(*off) - p0
+            if periodic:
+                d -= torch.round(d)
+            vs.append(p0 + d)
+        out.append(torch.stack(vs, 1))
+    return torch.cat(out, 0) * scale
+
+
+def density_floor_cells(verts, m_t, cell_index, n_cells):
+    """Per cell: the mass of a whole cell at the density of the densest tetrahedron whose
+    bounding box covers it (the per-cell floor of the relative error of sparse deposits: a
+    cell holding only a sliver of one tetrahedron carries the clip's absolute error at that
+    tetrahedron's density).  verts: [T, 4, 3] in cells; cell_index(ix, iy, iz) -> flat index
+    into the n_cells outputs, or -1 for cells not compared."""
+    import itertools
+
+    import torch
+    e1, e2, e3 = verts[:, 1] - verts[:, 0], verts[:, 2] - verts[:, 0], verts[:, 3] - verts[:, 0]
+    vol = torch.abs((e1 * torch.cross(e2, e3, dim=1)).sum(1)) / 6.0
+    keep = vol > 0
+    verts, dens = verts[keep], m_t / vol[keep]
+    lo = torch.floor(verts.min(1).values).long()
+    dim = torch.floor(verts.max(1).values).long() - lo + 1
+    floor = torch.zeros(n_cells, dtype=torch.float64, device=verts.device)
+    dmax = int(dim.max().item()) if dim.numel() else 0
+    for dx, dy, dz in itertools.product(range(dmax), repeat=3):
+        ok = (dim[:, 0] > dx) & (dim[:, 1] > dy) & (dim[:, 2] > dz)
+        if not bool(ok.any()):
+            continue
+        c = lo[ok] + torch.tensor([dx, dy, dz], device=lo.device)
+        idx = cell_index(c[:, 0], c[:, 1], c[:, 2])
+        sel = idx >= 0
+        floor.scatter_reduce_(0, idx[sel], dens[ok][sel], reduce="amax")
+    return floor
+
+
+def block_floor(pos_np, m, gl, box, n, dev):
+    """density_floor_cells of one open m^3 sample block on its gl^3 grid ([z, y, x] flat)."""
+    import torch
+    pos = torch.from_numpy(pos_np).to(dev)
+    cubes = torch.arange((m - 1) ** 3, device=dev)
+    v = lattice_tets_cells(pos, (m, m, m), cubes, gl / box, periodic=False)
+
+    def index(ix, iy, iz):
+        inside = (ix >= 0) & (ix < gl) & (iy >= 0) & (iy < gl) & (iz >= 0) & (iz < gl)
+        return torch.where(inside, ix + gl * (iy + gl * iz), torch.full_like(ix, -1))
+    return density_floor_cells(v, 1.0 / (6 * n ** 3), index, gl ** 3).cpu().numpy()
+
+
+def octree_subset_floor(pos, n, cube_ids, octree, touched):
+    """density_floor_cells of the cubes `cube_ids` of the periodic n^3 lattice over the leaf blocks
+    `touched` of `octree` ([len(touched), bc^3] flat), when all of them are at the finest level;
+    else None."""
+    import torch
+    leaves = torch.from_numpy(octree.leaves()).to(pos.device)
+    ml, bc = octree.max_level, octree.bc
+    if not bool((leaves[touched, 0] == ml).all()):
+        return None
+    side = 1 << ml
+    g = bc * side
+    leaf_of = torch.full((side ** 3,), -1, dtype=torch.long, device=pos.device)
+    fin = leaves[:, 0] == ml
+    lid = torch.nonzero(fin).ravel()
+    lv = leaves[fin].long()
+    leaf_of[lv[:, 1] + side * (lv[:, 2] + side * lv[:, 3])] = lid
+    pos_of = torch.full((leaves.shape[0],), -1, dtype=torch.long, device=pos.device)
+    pos_of[touched] = torch.arange(touched.numel(), device=pos.device)
+    v = lattice_tets_cells(pos, (n, n, n), cube_ids, float(g), periodic=True)
+
+    def index(ix, iy, iz):
+        ix, iy, iz = ix % g, iy % g, iz % g
+        lf = leaf_of[ix // bc + side * (iy // bc + side * (iz // bc))]
+        p = torch.where(lf >= 0, pos_of[lf.clamp(min=0)], torch.full_like(lf, -1))
+        loc = (ix % bc) + bc * ((iy % bc) + bc * (iz % bc))
+        return torch.where(p >= 0, p * bc ** 3 + loc, torch.full_like(p, -1))
+    return density_floor_cells(v, 1.0 / (6 * n ** 3), index, touched.numel() * bc ** 3).cpu().numpy()
+
+
 def gpu_blocks_error(pse, blocks, grids, m, n, dev, g_fine):
     """The GPU's FP32 deposit of the oracle's sample blocks against the oracle, cell by cell."""
     import numpy as np
     import torch
     from paper_1612_09491_gb300.metrics import cell_errors
-    fast, ref = [], []
+    fast, ref, flo = [], [], []
     for (pos, gl, box), g in zip(blocks, grids):
         d = torch.from_numpy(pos).to(dev)
         out = pse.deposit_uniform(d, (m, m, m), gl, box=box, periodic=False, particle_mass=1.0 / n ** 3,
                                   precision=pse.PSE_FP32_FP64ACC, schedule=pse.PSE_WARP_COOPERATIVE)
         fast.append(out.cpu().numpy().ravel())
         ref.append(g.ravel())
-    fast, ref = np.concatenate(fast), np.concatenate(ref)
+        flo.append(block_floor(pos, m, gl, box, n, dev))
+    fast, ref, flo = np.concatenate(fast), np.concatenate(ref), np.concatenate(flo)
     mean_cell = 1.0 / g_fine ** 3  # the full deposit's mean cell mass
-    e = cell_errors(fast, ref, floor_mass=1e-3 * mean_cell)
+    e = cell_errors(fast, ref, floor_mass=flo)
+    e["floor"] = ("per cell: a whole cell at the density of the densest tetrahedron whose bounding box "
+                  "covers it (sparse deposits: each block is deposited alone)")
     filled = ref >= 0.5 * mean_cell
-    e["floor"] = "1e-3 of the full deposit's mean cell mass"
     e["on_filled_cells"] = cell_errors(fast[filled], ref[filled])
     e["filled_cells"] = int(filled.sum())
+    e["with_mean_cell_floor"] = cell_errors(fast, ref, floor_mass=1e-3 * mean_cell)["max_rel"]
     e["sample"] = "the cpu_baseline blocks, deposited alone on both sides"
     return e
 
@@ -532,10 +643,17 @@ def run_scale(args, cfg):
                     "fp32_ms_on_sample": fms, "sample": "64 x 64 x 32 contiguous cubes",
                     "speedup": value / (6 * ids.numel() / (bms * 1e-3)),
                     "speedup_on_sample": bms / fms,
-                    "error_of_timed_arm_on_sample": cell_errors(fast, slow, floor_mass=1e-3 / cells),
-                    "error_floor": "1e-3 of the full deposit's mean cell mass",
                     "error_on_filled_cells": cell_errors(fast[filled], slow[filled]),
                     "filled_cells": int(filled.sum()), "leaves_compared": int(touched.numel())}
+            flo = octree_subset_floor(pos_d, n, ids, o, touched)
+            if flo is not None:
+                base["error_of_timed_arm_on_sample"] = cell_errors(fast, slow, floor_mass=flo.reshape(fast.shape))
+                base["error_floor"] = ("per cell: a whole cell at the density of the densest tetrahedron whose "
+                                       "bounding box covers it (the sample is a sparse deposit)")
+            else:
+                base["error_of_timed_arm_on_sample"] = cell_errors(fast, slow, floor_mass=1e-3 / cells)
+                base["error_floor"] = "1e-3 of the full deposit's mean cell mass"
+            base["with_mean_cell_floor"] = cell_errors(fast, slow, floor_mass=1e-3 / cells)["max_rel"]
             del pos_d
         cpu = oracle_err = None
         if not args.no_cpu:
@@ -570,7 +688,8 @@ def run_scale(args, cfg):
             "clips_per_s": world * st["partial_clips"] / (ms * 1e-3),
             "step_parts_ms": {"octree_build": sum(build_ms) / len(build_ms), "deposit": kern},
             "counters": {k: st[k] for k in ("tets", "bbox_cells", "inside_cells", "partial_clips", "fp64_redos",
-                                            "degenerate_tets", "single_cell_tets", "inverted_tets")},
+                                            "degenerate_tets", "single_cell_tets", "inverted_tets",
+                                            "column_runs")},
             "tet_sizes": tet_sizes,
             "mass_error": mass_error,
             "fp64_gpu_baseline": base,

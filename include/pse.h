@@ -69,7 +69,7 @@ extern "C" {
 
 /* precision (pse_deposit_opts.precision) */
 #define PSE_FP64_PLAIN 0   /* every step in float64 */
-#define PSE_FP32_FP64ACC 1 /* float32 clip with float64 redo of guarded clips; float64 accumulation */
+#define PSE_FP32_FP64ACC 1 /* float32 clip; float64 clip of guarded tetrahedra; float64 accumulation */
 #define PSE_FP32_COMPENSATED 2 /* the float32 clip of PSE_FP32_FP64ACC; each cell sums its deposits as a
                                   float32 pair (hi, lo) with an error-free two-sum on every add, held in
                                   the cell's own 8 output bytes and turned into float64 hi + lo at the
@@ -109,8 +109,9 @@ typedef struct pse_deposit_opts {
                                 of those whose bounding box exceeds split_cells cells (lattice deposits
                                 need pse_workspace_size(PSE_OP_DEPOSIT_UNIFORM, lat, opts) bytes) */
     const void *tuning;      /* nullable host pointer to a pse_tuning block; NULL = built-in defaults */
-    double guard_eps;        /* FP32 clip guard: redo a tetrahedron's clips in float64 when the
-                                estimated relative error of its FP32 clip exceeds guard_eps (<=0: default) */
+    double guard_eps;        /* FP32 clip guard: clip a tetrahedron in float64, from its exact vertices,
+                                when the estimated relative error of its FP32 clip exceeds guard_eps
+                                (<=0: default) */
     int64_t spin_limit;      /* iteration bound of every device-side wait (<=0: default) */
     int32_t accumulate;      /* 0: the call overwrites the output; 1: it adds to it */
     int32_t mass_fixup;      /* FP32 path with accumulate = 0: 1 rescales the call's output by
@@ -130,7 +131,9 @@ typedef struct pse_deposit_stats {
     uint64_t bbox_cells;       /* (tetrahedron, cell) pairs inside bounding boxes */
     uint64_t inside_cells;     /* pairs classified "cell inside tetrahedron" */
     uint64_t partial_clips;    /* pairs that went through the exact clip */
-    uint64_t fp64_redos;       /* clips re-done in float64 by the guard */
+    uint64_t fp64_redos;       /* partial cells of guarded tetrahedra, clipped in float64 (the warp
+                                  schedules clip them by column runs in a pass of their own; the
+                                  others re-clip each such cell in float64) */
     uint64_t degenerate_tets;  /* zero-volume tetrahedra (centroid rule) */
     uint64_t single_cell_tets; /* tetrahedra whose bounding box is one cell */
     uint64_t bin_counts[8];    /* binned schedule: tetrahedra per size bin */

@@ -3,7 +3,7 @@
 // and the warp-cooperative (tetrahedron, cell) pair machinery.
 #pragma once
 
-#include "geom.cuh"
+#include "column.cuh"
 #include "internal.h"
 
 namespace pse {
@@ -161,12 +161,17 @@ __device__ __forceinline__ void exact_vertices(const P3<float> (&v)[4], const P3
                            ((double)v[q].z + (double)r[q].z) - (double)cz);
 }
 
-// |6V| of the exact tetrahedron (falls back to the float32 one if that is 0)
-__device__ __forceinline__ double exact_vol6(const P3<float> (&v)[4], const P3<float> (&r)[4], double vol6_f32)
+// |6V| of the exact tetrahedron (falls back to the float32 one if that is 0); flip is set
+// when the exact tetrahedron's orientation is the opposite of the float32 one's (a sliver
+// thinner than float32 rounding can turn over when rounded)
+__device__ __forceinline__ double exact_vol6(const P3<float> (&v)[4], const P3<float> (&r)[4], double vol6_f32,
+                                             bool *flip = nullptr)
 {
     P3<double> pd[4];
     exact_vertices(v, r, 0, 0, 0, pd);
-    const double d = fabs(det6(pd));
+    const double s = det6(pd);
+    if (flip) *flip = s < 0.0;
+    const double d = fabs(s);
     return d > 0.0 ? d : vol6_f32;
 }
 
@@ -366,18 +371,21 @@ struct WarpSmem {
     float rho[32];        // 6 m_t / |6V| (deposit = rho * overlap volume, formed in float32)
     int start[32];        // exclusive prefix of the pair counts
     int skip[32];         // first pair of this record (split tetrahedra; else 0)
-    int guard[32];        // 1: clip this tetrahedron in float64
+    int guard[32];        // bit 0: a guarded tetrahedron (clipped in float64);
+                          // kGuardFlip: its exact vertices are oriented the other way round
     int cut[32];          // octree: 1 if the record's cell range starts above the tetrahedron's
                           // own first layer along its divergence axis (a leaf block cuts it)
     float *vres;          // this warp's residual block in global memory: [12][32] floats, the
                           // rounding residuals of guarded records (exact vertex = v + vres)
     unsigned long long q[64];  // queued partial pairs: t | ix << 5 | iy << 24 | iz << 43
     unsigned long long gq[64]; // queued partial pairs of guarded tetrahedra (float64 clips)
+    double2 *dpoly;            // the guarded pass's float64 edge slots: [21][32], this warp's
     float2 poly[21][32];       // FP32 clip: each lane's 7 edge slots, 3 float2 each:
                                // (a.x, a.y), (a.z, b.x), (b.y, b.z)
 };
 
 constexpr int kQBits = 19;  // per-axis cell offset bits in a queue entry
+constexpr int kGuardFlip = 2;
 constexpr unsigned long long kQMask = (1ull << kQBits) - 1;
 
 __device__ __forceinline__ unsigned long long q_pack(int t, int ix, int iy, int iz)
@@ -446,12 +454,13 @@ __device__ __forceinline__ void store_record(WarpSmem *S, int lane, const TetSet
         S->base[a][lane] = base[a];
     }
     const int guard = (ts.kappa <= kappa_max) ? 0 : 1;
-    S->rho[lane] = guard ? (float)(6.0 * m_t / exact_vol6(ts.v, res, ts.vol6))
+    bool flip = false;
+    S->rho[lane] = guard ? (float)(6.0 * m_t / exact_vol6(ts.v, res, ts.vol6, &flip))
                          : __fdiv_rn((float)(6.0 * m_t), (float)ts.vol6);
     S->lx[lane] = ts.lx;
     S->ly[lane] = ts.ly;
     S->axis[lane] = ts.axis;
-    S->guard[lane] = guard;
+    S->guard[lane] = guard | (flip ? kGuardFlip : 0);
     S->skip[lane] = skip;
     S->cut[lane] = 0;
     if (guard) store_residuals(S, lane, res);
@@ -521,6 +530,34 @@ struct RecordRun {
     __device__ __forceinline__ P3<float> nrm(int f) const
     {
         return to_axis(mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]), C);
+    }
+};
+
+// Guarded record t as the guarded pass's column clip reads it: the exact vertices (float32
+// vertex plus its rounding residual) in float64, in the exact tetrahedron's positive
+// orientation, relative to the run's first cell and relabelled so that axis C is z; the
+// outward face normals are formed from them when asked for.  (v - f is exact: both are
+// float32 values a few cells apart.)
+struct RecordRun64 {
+    const WarpSmem *S;
+    int t, C;
+    float fx, fy, fz;
+    bool flip;
+    __device__ __forceinline__ double co(int row, float f) const
+    {
+        return ((double)S->v[row][t] - (double)f) + (double)S->vres[row * 32 + t];
+    }
+    __device__ __forceinline__ P3<double> vtx(int i) const
+    {
+        const int k = flip ? (i == 1 ? 2 : (i == 2 ? 1 : i)) : i;
+        return to_axis(mk<double>(co(3 * k, fx), co(3 * k + 1, fy), co(3 * k + 2, fz)), C);
+    }
+    __device__ __forceinline__ P3<double> nrm(int f) const
+    {
+        int a, b, c;
+        face_vertices(f, a, b, c);
+        const P3<double> pa = vtx(a);
+        return cross(sub(vtx(b), pa), sub(vtx(c), pa));
     }
 };
 
@@ -608,10 +645,11 @@ __device__ __forceinline__ void clip_round(const DepositParams &P, WarpSmem *S, 
     __syncwarp();
 }
 
-// Column clips of the first `count` entries of S->q (runs of unguarded tetrahedra), one run
-// per lane.  (Dealing the (run, face) jobs and the level fans out over the warp raised the
-// active lanes but cost more in shuffles and reloads than it saved: 12% slower.)
-template <bool STATS, bool OCT, Acc A>
+// Column clips of the first `count` entries of S->q, one run per lane: in float32 (T = float,
+// the records below the guard) or in float64 from the exact vertices (T = double, the
+// guarded records).  (Dealing the (run, face) jobs and the level fans out over the warp
+// raised the active lanes but cost more in shuffles and reloads than it saved: 12% slower.)
+template <bool STATS, bool OCT, Acc A, class T>
 __device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, int count, int lane, Counters &cnt)
 {
     if (lane < count) {
@@ -621,10 +659,19 @@ __device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, i
         const int C = S->axis[t];
         int cx, cy, cz, kw;
         run_cells(S, t, (int)((ent >> 5) & kQMask), (int)((ent >> (5 + kQBits)) & kQMask), w, cx, cy, cz, kw);
-        const RecordRun src{S, t, C, (float)cx, (float)cy, (float)cz};
         if (STATS) cnt.u[ST_RUNS]++;
-        float vol[kRun];
-        column_volumes<kRun>(src, S->lx[t], S->ly[t], kw, w > 0 || S->cut[t] != 0, vol, &S->poly[0][lane]);
+        const bool lo_open = w > 0 || S->cut[t] != 0;
+        double vol[kRun];
+        if constexpr (sizeof(T) == sizeof(float)) {
+            const RecordRun src{S, t, C, (float)cx, (float)cy, (float)cz};
+            float v32[kRun];
+            column_volumes<kRun>(src, S->lx[t], S->ly[t], kw, lo_open, v32, &S->poly[0][lane]);
+#pragma unroll
+            for (int j = 0; j < kRun; ++j) vol[j] = v32[j];
+        } else {
+            const RecordRun64 src{S, t, C, (float)cx, (float)cy, (float)cz, (S->guard[t] & kGuardFlip) != 0};
+            column_volumes<kRun>(src, (double)S->lx[t], (double)S->ly[t], kw, lo_open, vol, S->dpoly + lane);
+        }
         const float rho = S->rho[t];
 #pragma unroll
         for (int j = 0; j < kRun; ++j) {
@@ -641,12 +688,16 @@ __device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, i
                     ng[f] = S->neg[f][t];
                 }
                 const int cls = classify_cell<float>(n, e, ps, ng, (float)ex, (float)ey, (float)ez);
-                if (cls == CELL_PARTIAL) cnt.u[ST_PARTIAL_CLIPS]++;
-                else if (cls == CELL_INSIDE) cnt.u[ST_INSIDE_CELLS]++;
+                if (cls == CELL_PARTIAL) {
+                    cnt.u[ST_PARTIAL_CLIPS]++;
+                    if (sizeof(T) != sizeof(float)) cnt.u[ST_FP64_REDOS]++;
+                } else if (cls == CELL_INSIDE) {
+                    cnt.u[ST_INSIDE_CELLS]++;
+                }
             }
-            if (j < kw && vol[j] > 0.f) {
+            if (j < kw && vol[j] > 0.0) {
                 if (STATS) cnt.u[ST_OVERLAPPED]++;
-                const double m = (double)(rho * vol[j]);
+                const double m = (sizeof(T) == sizeof(float)) ? (double)(rho * (float)vol[j]) : (double)rho * vol[j];
                 cnt.add_dep(m);
                 if (!deposit_pair<OCT, A>(P, S, t, ex, ey, ez, m) && STATS) cnt.dropped += m;
             }
@@ -674,8 +725,8 @@ __device__ __forceinline__ void redo_round(const DepositParams &P, WarpSmem *S, 
 //  * kPassAll: records on both sides of the guard, enumerated by cells; FP32 clips and FP64
 //    clips in the same kernel (the warp-per-tetrahedron baseline);
 //  * kPassFp32: records below the guard only, enumerated by column runs (FP32 column clips);
-//  * kPassGuard: guarded records only, enumerated by cells (FP64 clips from the exact
-//    vertices).
+//  * kPassGuard: guarded records only, enumerated by column runs (FP64 column clips from
+//    the exact vertices).
 // The warp-cooperative and octree schedules run kPassFp32 and then kPassGuard over the same
 // tetrahedra, so neither kernel carries the other's clip code or registers.
 enum { kPassAll = 0, kPassFp32 = 1, kPassGuard = 2 };
@@ -686,9 +737,9 @@ enum { kPassAll = 0, kPassFp32 = 1, kPassGuard = 2 };
 template <bool STATS, bool OCT, Acc A, int PASS>
 __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, int lane, int npairs, Counters &cnt)
 {
-    constexpr bool COL = PASS == kPassFp32;
-    constexpr bool HAS_Q = PASS != kPassGuard;
-    constexpr bool HAS_GQ = PASS != kPassFp32;
+    constexpr bool COL = PASS != kPassAll;  // both passes of the warp schedules clip column runs
+    constexpr bool HAS_Q = true;
+    constexpr bool HAS_GQ = PASS == kPassAll;
     const unsigned lt_mask = (1u << lane) - 1u;
     int incl = npairs;
 #pragma unroll
@@ -775,7 +826,8 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
         if constexpr (HAS_Q) {
             if (qn >= 32 || (last && qn > 0)) {
                 const int take = qn >= 32 ? 32 : qn;
-                if constexpr (COL) run_round<STATS, OCT, A>(P, S, take, lane, cnt);
+                if constexpr (PASS == kPassFp32) run_round<STATS, OCT, A, float>(P, S, take, lane, cnt);
+                else if constexpr (PASS == kPassGuard) run_round<STATS, OCT, A, double>(P, S, take, lane, cnt);
                 else clip_round<STATS, OCT, A>(P, S, take, lane, cnt);
                 if (lane < qn - take) S->q[lane] = S->q[take + lane];
                 qn -= take;
@@ -797,11 +849,25 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
 }
 
 
-// Point S->vres at this warp's residual block (every lane writes the same value).
-__device__ __forceinline__ void bind_residuals(const DepositParams &P, WarpSmem *S)
+// Point S->vres at this warp's residual block and, in the guarded pass, S->dpoly at its
+// float64 edge slots, which follow the blocks' WarpSmem array in dynamic shared memory
+// (every lane writes the same values).
+__device__ __forceinline__ void bind_residuals(const DepositParams &P, WarpSmem *S, bool guard_slots = false)
 {
     S->vres = P.vres + ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (12 * 32);
+    if (guard_slots) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        double2 *base = reinterpret_cast<double2 *>(smem_raw + (blockDim.x >> 5) * sizeof(WarpSmem));
+        S->dpoly = base + (threadIdx.x >> 5) * (21 * 32);
+    }
     __syncwarp();
+}
+
+// dynamic shared memory of a warp kernel with `warps` warps: the WarpSmem array, plus the
+// float64 edge slots in the guarded pass
+inline size_t warp_smem_bytes(int warps, bool guard_slots)
+{
+    return sizeof(WarpSmem) * warps + (guard_slots ? sizeof(double2) * 21 * 32 * warps : 0);
 }
 
 inline int persistent_blocks(const void *kernel, int threads, size_t smem)

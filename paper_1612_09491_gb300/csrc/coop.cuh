@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
     constexpr bool FIRST = PASS == kPassFp32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
-    bind_residuals(P, S);
+    bind_residuals(P, S, !FIRST);
     const int lane = threadIdx.x & 31;
     Counters cnt;
     if (STATS) cnt.zero();
@@ -200,9 +200,9 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                         store_record(S, lane, ts, res, base, m_t, P.kappa_max, 0);
                     }
                 } else {
-                    // guarded: cells, clipped in FP64 from the exact vertices (the float32
-                    // vertices plus their rounding residuals)
-                    npairs = (int)ncell;
+                    // guarded: column runs, clipped in float64 from the exact vertices
+                    // (the float32 vertices plus their rounding residuals)
+                    npairs = (int)run_count(ts.dim, ts.axis);
                     P3<float> res[4], v2[4];
                     int b2[3];
                     if (P.src == SRC_TETS) explicit_tet<float>(P, unit, v2, b2, res);
@@ -228,12 +228,19 @@ cudaError_t launch_coop_pass(const DepositParams &p, bool stats, int blocks_per_
     // SM), 3 (170 registers, 12 warps) or 4 (128 registers, 16 warps).  The counting
     // variant (stats) is built for 2 only.
     const int threads = kCoopThreads;
-    const size_t smem = sizeof(WarpSmem) * (threads / 32);
-    const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
-    const void *k = stats ? (const void *)k_warp_coop<true, 2, BINNED, A, PASS>
-                    : minb == 4 ? (const void *)k_warp_coop<false, 4, BINNED, A, PASS>
-                    : minb == 3 ? (const void *)k_warp_coop<false, 3, BINNED, A, PASS>
-                                : (const void *)k_warp_coop<false, 2, BINNED, A, PASS>;
+    constexpr bool GUARD = PASS == kPassGuard;
+    const size_t smem = warp_smem_bytes(threads / 32, GUARD);
+    // the guarded pass (190 registers, float64 slots) runs 2 blocks per SM
+    const int minb = (stats || GUARD) ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
+    const void *k;
+    if constexpr (GUARD) {
+        k = stats ? (const void *)k_warp_coop<true, 2, BINNED, A, PASS> : (const void *)k_warp_coop<false, 2, BINNED, A, PASS>;
+    } else {
+        k = stats ? (const void *)k_warp_coop<true, 2, BINNED, A, PASS>
+            : minb == 4 ? (const void *)k_warp_coop<false, 4, BINNED, A, PASS>
+            : minb == 3 ? (const void *)k_warp_coop<false, 3, BINNED, A, PASS>
+                        : (const void *)k_warp_coop<false, 2, BINNED, A, PASS>;
+    }
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);

@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(128) k_bin_pass(const DepositParams P)
                 tet_setup<float>(v, ts);
                 ncell = (int64_t)ts.dim[0] * ts.dim[1] * ts.dim[2];
                 cand = tet_ok(base, ts) && ts.vol6 != 0.0 && ncell > 1 && ncell <= (int64_t)INT32_MAX;
-                // the work items count pairs: column runs below the guard, cells above it
-                if (cand) npair = (ts.kappa <= P.kappa_max) ? run_count(ts.dim, ts.axis) : ncell;
+                // the work items count pairs: column runs (both passes clip runs)
+                if (cand) npair = run_count(ts.dim, ts.axis);
                 if (MODEL && cand) tet_features(ts, f);
             }
         }
@@ -420,7 +420,7 @@ cudaError_t launch_warp_coop(const DepositParams &p, bool stats, int blocks_per_
 cudaError_t launch_warp_per_tet(const DepositParams &p, bool stats, cudaStream_t st)
 {
     const int threads = kCoopThreads;
-    const size_t smem = sizeof(WarpSmem) * (threads / 32);
+    const size_t smem = warp_smem_bytes(threads / 32, false);
     const void *k = stats ? (const void *)k_warp_per_tet<true> : (const void *)k_warp_per_tet<false>;
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;

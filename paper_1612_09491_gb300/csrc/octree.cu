@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
     constexpr bool FIRST = PASS == kPassFp32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
-    bind_residuals(P, S);
+    bind_residuals(P, S, !FIRST);
     const int lane = threadIdx.x & 31;
     Counters cnt;
     if (STATS) cnt.zero();
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                 // left to the guarded pass; counted here
                                 if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
                             } else if (ncell > 0) {
-                                npairs = FIRST ? (int)run_count(dim, ts.axis) : (int)ncell;
+                                npairs = (int)run_count(dim, ts.axis);
                                 if (STATS && FIRST) {
                                     cnt.u[ST_BBOX_CELLS] += ncell;
                                     cnt.u[ST_BIN0 + size_bin(ncell)]++;
@@ -472,12 +472,13 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                     S->base[a][lane] = base[a];
                                 }
                                 S->leaf[lane] = hit.leaf;
-                                S->rho[lane] = guard ? (float)(6.0 * m_t / exact_vol6(ts.v, res, ts.vol6))
+                                bool flip = false;
+                                S->rho[lane] = guard ? (float)(6.0 * m_t / exact_vol6(ts.v, res, ts.vol6, &flip))
                                                      : __fdiv_rn((float)(6.0 * m_t), (float)ts.vol6);
                                 S->lx[lane] = ts.lx;
                                 S->ly[lane] = ts.ly;
                                 S->axis[lane] = ts.axis;
-                                S->guard[lane] = guard ? 1 : 0;
+                                S->guard[lane] = guard ? (1 | (flip ? kGuardFlip : 0)) : 0;
                                 S->skip[lane] = 0;
                                 {
                                     const int C = ts.axis;
@@ -794,16 +795,24 @@ cudaError_t launch_oct_pass(const DepositParams &p, bool stats, int blocks_per_s
     // blocks_per_sm resident blocks of 128 threads: 2 (255 registers), 3 (170) or 4 (128);
     // the counting variant (stats) is built for 2 only
     const int threads = 128;
-    const size_t smem = sizeof(WarpSmem) * (threads / 32);
-    const int minb = stats ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
-    const void *k = p.comp ? (stats ? (const void *)k_oct_warp<true, 2, Acc::COMP, PASS>
-                              : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::COMP, PASS>
-                              : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::COMP, PASS>
-                                          : (const void *)k_oct_warp<false, 2, Acc::COMP, PASS>)
-                    : (stats ? (const void *)k_oct_warp<true, 2, Acc::F64, PASS>
-                       : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::F64, PASS>
-                       : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::F64, PASS>
-                                   : (const void *)k_oct_warp<false, 2, Acc::F64, PASS>);
+    constexpr bool GUARD = PASS == kPassGuard;
+    const size_t smem = warp_smem_bytes(threads / 32, GUARD);
+    // the guarded pass (190 registers, float64 slots) runs 2 blocks per SM
+    const int minb = (stats || GUARD) ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
+    const void *k;
+    if constexpr (GUARD) {
+        k = p.comp ? (stats ? (const void *)k_oct_warp<true, 2, Acc::COMP, PASS> : (const void *)k_oct_warp<false, 2, Acc::COMP, PASS>)
+                   : (stats ? (const void *)k_oct_warp<true, 2, Acc::F64, PASS> : (const void *)k_oct_warp<false, 2, Acc::F64, PASS>);
+    } else {
+        k = p.comp ? (stats ? (const void *)k_oct_warp<true, 2, Acc::COMP, PASS>
+                      : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::COMP, PASS>
+                      : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::COMP, PASS>
+                                  : (const void *)k_oct_warp<false, 2, Acc::COMP, PASS>)
+            : (stats ? (const void *)k_oct_warp<true, 2, Acc::F64, PASS>
+               : minb == 4 ? (const void *)k_oct_warp<false, 4, Acc::F64, PASS>
+               : minb == 3 ? (const void *)k_oct_warp<false, 3, Acc::F64, PASS>
+                           : (const void *)k_oct_warp<false, 2, Acc::F64, PASS>);
+    }
     cudaError_t err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int blocks = persistent_blocks(k, threads, smem);

@@ -26,7 +26,7 @@ HARNESS = r'''
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
-#include "geom.cuh"
+#include "column.cuh"
 using namespace pse;
 
 static float urand(unsigned long long &s)
@@ -48,7 +48,7 @@ static void run(const TetSetup<float> &ts, int ia, int ib, int w0, int K, float 
         p[q] = to_axis(mk<float>(ts.v[q].x - cell[0], ts.v[q].y - cell[1], ts.v[q].z - cell[2]), ax);
         na[q] = to_axis(ts.n[q], ax);
     }
-    const TetArrays src{p, na};
+    const TetArrays<float> src{p, na};
     column_volumes<KW>(src, ts.lx, ts.ly, K, w0 > 0, vol, E);
 }
 
