@@ -697,6 +697,11 @@ def run_scale(args, cfg):
             "kernel_ms": kern,
             "roofline": roof,
             "issue": issue,
+            "atomics": {"reductions_per_s": st["overlapped_cells"] / (kern * 1e-3),
+                        "peak_per_s": peaks["red_f64_per_s"],
+                        "frac": st["overlapped_cells"] / (kern * 1e-3) / peaks["red_f64_per_s"],
+                        "note": "one red.global.add.f64 per (tetrahedron, cell) pair that received mass, against "
+                                "pse_microbench_red (pseudo-random FP64 reductions over a 134 MB array)"},
             "cpu_baseline": cpu,
             "e2e": {"value": world * n_tets / (e2e_mean * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": hist_bytes + 8, "ms_per_step": e2e_mean, "steps": len(e2e_ms),
@@ -704,7 +709,9 @@ def run_scale(args, cfg):
                             f"(z-slabs of {SLAB} cube layers, double-buffered), then the total mass read back; "
                             "the leaf blocks stay on the GPU",
                     "total_mass": float(mass_h.item())},
-            "gpu_launches": 3 * args.steps,
+            # per step: k_tet_size_hist, the two k_oct_warp passes, k_finish (the ncu launch list
+            # of this command in profiles/)
+            "gpu_launches": 4 * args.steps,
             "clocks": clk.summary(),
             "wall_s_timed": t_wall,
             **extra,

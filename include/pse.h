@@ -178,7 +178,12 @@ typedef struct pse_tuning {
     int32_t chunk_cells;     /* binned schedule: bounding-box cells per split work item; <= 0: default 512 */
     int32_t use_graph;       /* with a caller workspace and h_stats NULL: 1 = replay the call's launch
                                 sequence as a CUDA graph (captured once per distinct argument set) */
-    int32_t reserved[5];
+    int32_t guard_list_cap;  /* warp and octree schedules: the FP32 pass lists the guarded tetrahedra
+                                (at most 4,194,304 per call, or per slab when streamed) so that the
+                                guarded pass visits only them; when more are guarded it scans every
+                                tetrahedron again.  0: the full list; > 0: a smaller capacity; < 0: no
+                                list (always scan again).  Results are the same either way. */
+    int32_t reserved[4];
 } pse_tuning;
 
 /*

@@ -81,6 +81,7 @@ def opts(precision: int = PSE_FP32_FP64ACC, schedule: int = PSE_WARP_COOPERATIVE
         tu.split_cells = int(tuning.get("split_cells", 0))
         tu.chunk_cells = int(tuning.get("chunk_cells", 0))
         tu.use_graph = int(tuning.get("use_graph", 0))
+        tu.guard_list_cap = int(tuning.get("guard_list_cap", 0))
         _keep[:] = [tu]
         o.tuning = ctypes.cast(ctypes.pointer(tu), ctypes.c_void_p).value
     o.precision = precision

@@ -104,7 +104,7 @@ class Octree(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("split_cells", ctypes.c_int32), ("chunk_cells", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("guard_list_cap", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class PseError(RuntimeError):

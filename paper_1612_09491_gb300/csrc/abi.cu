@@ -233,23 +233,26 @@ constexpr int kDefaultSplitCells = 1024;
 constexpr int kDefaultChunkCells = 512;
 
 // workspace of a deposit; n_tets < 0: unknown (0 is returned if it matters)
-// [Workspace header][warp kernels: residual blocks][binned: queue][cost model: bitmap]
+// [Workspace header][warp kernels: residual blocks, guarded-tetrahedron list][binned: queue]
+// [cost model: bitmap]
 size_t deposit_ws_bytes(const pse_deposit_opts *o, int64_t n_tets)
 {
     const int sched = o ? o->schedule : PSE_WARP_COOPERATIVE;
     if (sched == PSE_THREAD_PER_TET) return pse::kWorkspaceBytes;
-    const size_t base = pse::kWorkspaceBytes + pse::kResidualBytes;
+    const size_t base = pse::kWorkspaceBytes + pse::kResidualBytes + pse::kGuardListBytes;
     if (sched != PSE_BINNED_PERSISTENT) return base;
     if (!o->cost_model) return base + pse::kQueueBytes;
     if (n_tets < 0) return 0;
     return base + pse::kQueueBytes + pse::qbits_bytes(n_tets);
 }
 
-// octree deposits: the header, plus the residual blocks for the warp kernel
+// octree deposits: the header, plus the residual blocks and the guarded-tetrahedron list for
+// the warp kernel
 size_t octree_ws_bytes(const pse_deposit_opts *o)
 {
-    return (o && o->schedule == PSE_THREAD_PER_TET) ? pse::kWorkspaceBytes
-                                                     : pse::kWorkspaceBytes + pse::kResidualBytes;
+    return (o && o->schedule == PSE_THREAD_PER_TET)
+               ? pse::kWorkspaceBytes
+               : pse::kWorkspaceBytes + pse::kResidualBytes + pse::kGuardListBytes;
 }
 
 // h_pos != NULL: stream the lattice from host memory in z-slabs of slab_cubes cube layers
@@ -271,8 +274,14 @@ int run_deposit(pse::DepositParams &p, const pse_deposit_opts &o, int64_t cells,
     p.ws = lease.ws;
     if (o.schedule != PSE_THREAD_PER_TET)
         p.vres = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes);
-    unsigned char *const after_res = reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes +
-                                     pse::kResidualBytes;
+    unsigned char *const list = reinterpret_cast<unsigned char *>(lease.ws) + pse::kWorkspaceBytes +
+                                pse::kResidualBytes;
+    unsigned char *const after_res = list + pse::kGuardListBytes;
+    if (o.schedule != PSE_THREAD_PER_TET) {
+        const int32_t cap = tu ? tu->guard_list_cap : 0;
+        p.guard_list = reinterpret_cast<int64_t *>(list);
+        p.guard_cap = cap < 0 ? 0 : (cap > 0 && cap < pse::kGuardListCap ? cap : pse::kGuardListCap);
+    }
     size_t qbits_len = 0;
     if (binned && o.cost_model) {
         p.model = static_cast<const pse::CostModelDev *>(o.cost_model);

@@ -143,7 +143,7 @@ __device__ __forceinline__ void explicit_tet(const DepositParams &P, int64_t t, 
 
 // The float32 vertices of the FP32 path are rounded; res holds the rounding residuals
 // (exact value = (double)v + (double)res, both terms exact in float64), so that the
-// guard's float64 redo and volume use the exact tetrahedron.
+// guarded float64 clips and volume use the exact tetrahedron.
 __device__ __forceinline__ void swap12(P3<float> (&r)[4])
 {
     const P3<float> t = r[1];
@@ -403,9 +403,9 @@ __device__ __forceinline__ void decompose(int local, int dx, int dy, int &ix, in
     ix = r - iy * dx;
 }
 
-// The float64 redo of a guarded clip of record t against cell (cx, cy, cz), kept out
-// of line so that the FP32 hot loop stays small; it rebuilds the exact vertices from
-// the float32 vertices and their residuals.
+// The float64 clip of guarded record t against cell (cx, cy, cz) in the cell-by-cell
+// schedule (the warp-per-tetrahedron baseline), kept out of line so that the FP32 hot loop
+// stays small; it rebuilds the exact vertices from the float32 vertices and their residuals.
 __device__ __noinline__ double redo_fp64(const WarpSmem *S, int t, int cx, int cy, int cz)
 {
     P3<float> v[4], r[4];
@@ -721,6 +721,37 @@ __device__ __forceinline__ void redo_round(const DepositParams &P, WarpSmem *S, 
     __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// The guarded-tetrahedron list.  The FP32 pass already sets up every tetrahedron; it lists
+// the guarded multi-cell ones so that the guarded pass visits only those instead of
+// generating and setting up every tetrahedron again (on a lattice with few guarded
+// tetrahedra that second scan was most of the guarded pass).
+// ---------------------------------------------------------------------------
+// Append the id of this lane's guarded tetrahedron (want) with one atomic per warp.  Ids past
+// the capacity are not stored, but the count still grows, which sends the guarded pass back
+// to a full scan.  Called by all 32 lanes.
+__device__ __forceinline__ void list_guarded(const DepositParams &P, bool want, int64_t id, int lane)
+{
+    const unsigned m = __ballot_sync(kFull, want);
+    if (m == 0u || P.guard_cap == 0) return;
+    unsigned long long first = 0;
+    if (lane == 0) first = atomicAdd(&P.ws->guard_count, (unsigned long long)__popc(m));
+    first = __shfl_sync(kFull, first, 0);
+    if (want) {
+        const unsigned long long k = first + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+        if (k < (unsigned long long)P.guard_cap) P.guard_list[k] = id;
+    }
+}
+
+// The guarded pass: the number of listed tetrahedra when the FP32 pass listed all of them,
+// else -1 (scan every tetrahedron).
+__device__ __forceinline__ int64_t listed_guarded(const DepositParams &P)
+{
+    if (P.guard_cap == 0) return -1;
+    const unsigned long long c = *reinterpret_cast<const volatile unsigned long long *>(&P.ws->guard_count);
+    return c > (unsigned long long)P.guard_cap ? -1 : (int64_t)c;
+}
+
 // Which records a kernel holds, and so which clips it carries:
 //  * kPassAll: records on both sides of the guard, enumerated by cells; FP32 clips and FP64
 //    clips in the same kernel (the warp-per-tetrahedron baseline);
@@ -849,26 +880,33 @@ __device__ __forceinline__ void coop_pairs(const DepositParams &P, WarpSmem *S, 
 }
 
 
+// Each warp's shared memory is a WarpSmem, except in the guarded pass: there the float64
+// edge slots ([21][32] double2) take the place of the FP32 ones (poly, the struct's last
+// member, which that pass never touches) and run past the struct's end, so a warp needs
+// 19 KB instead of 24 and three 4-warp blocks fit an SM.
+constexpr size_t kGuardWarpBytes = offsetof(WarpSmem, poly) + sizeof(double2) * 21 * 32;
+static_assert(offsetof(WarpSmem, poly) % 16 == 0 && kGuardWarpBytes % 16 == 0 && sizeof(WarpSmem) % 16 == 0,
+              "warp blocks of shared memory must keep 16-byte alignment");
+PSE_HD constexpr size_t warp_stride(bool guard_slots) { return guard_slots ? kGuardWarpBytes : sizeof(WarpSmem); }
+
+// this warp's block of dynamic shared memory
+__device__ __forceinline__ WarpSmem *warp_smem(bool guard_slots)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return reinterpret_cast<WarpSmem *>(smem_raw + (threadIdx.x >> 5) * warp_stride(guard_slots));
+}
+
 // Point S->vres at this warp's residual block and, in the guarded pass, S->dpoly at its
-// float64 edge slots, which follow the blocks' WarpSmem array in dynamic shared memory
-// (every lane writes the same values).
+// float64 edge slots (every lane writes the same values).
 __device__ __forceinline__ void bind_residuals(const DepositParams &P, WarpSmem *S, bool guard_slots = false)
 {
     S->vres = P.vres + ((size_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (12 * 32);
-    if (guard_slots) {
-        extern __shared__ __align__(16) unsigned char smem_raw[];
-        double2 *base = reinterpret_cast<double2 *>(smem_raw + (blockDim.x >> 5) * sizeof(WarpSmem));
-        S->dpoly = base + (threadIdx.x >> 5) * (21 * 32);
-    }
+    if (guard_slots) S->dpoly = reinterpret_cast<double2 *>(&S->poly[0][0]);
     __syncwarp();
 }
 
-// dynamic shared memory of a warp kernel with `warps` warps: the WarpSmem array, plus the
-// float64 edge slots in the guarded pass
-inline size_t warp_smem_bytes(int warps, bool guard_slots)
-{
-    return sizeof(WarpSmem) * warps + (guard_slots ? sizeof(double2) * 21 * 32 * warps : 0);
-}
+// dynamic shared memory of a warp kernel with `warps` warps
+inline size_t warp_smem_bytes(int warps, bool guard_slots) { return warp_stride(guard_slots) * warps; }
 
 inline int persistent_blocks(const void *kernel, int threads, size_t smem)
 {

@@ -69,13 +69,12 @@ constexpr int kCoopThreads = 128;
 
 // PASS kPassFp32 visits every tetrahedron: it counts them, deposits the degenerate and
 // single-cell ones, and clips those below the guard by column runs.  PASS kPassGuard visits
-// them again and clips only the guarded multi-cell ones, cell by cell in FP64.
+// them again and clips only the guarded multi-cell ones, by column runs in FP64.
 template <bool STATS, int MINB, bool BINNED, Acc A, int PASS>
 __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositParams P)
 {
     constexpr bool FIRST = PASS == kPassFp32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
+    WarpSmem *S = warp_smem(!FIRST);
     bind_residuals(P, S, !FIRST);
     const int lane = threadIdx.x & 31;
     Counters cnt;
@@ -91,6 +90,11 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
         n_chunks = split ? (int64_t)P.ws->n_chunk_items : 0;
         q = split ? min((int64_t)P.ws->queue_count, P.q_cap) : 0;
     }
+    // the guarded pass of the warp schedule: the tetrahedra the FP32 pass listed, 32 per item,
+    // when it listed all of them
+    const int64_t listed = (!FIRST && !BINNED) ? listed_guarded(P) : -1;
+    const bool LIST = listed >= 0;
+    const int64_t n_items = LIST ? (listed + 31) / 32 : P.n_items;
 
     for (;;) {
         unsigned long long item = 0;
@@ -99,14 +103,35 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
         const bool is_chunk = BINNED && (int64_t)item < n_chunks;
         if (!is_chunk) {
             item -= (unsigned long long)n_chunks;
-            if ((int64_t)item >= P.n_items) break;
+            if ((int64_t)item >= n_items) break;
         }
 
         // the 32 units (cubes or tetrahedra) of this item
         int64_t unit = -1;
         int64_t ci = 0, cj = 0, ck = 0;
+        int s_listed = 0;
         if (is_chunk) {
             // nothing: chunk_setup below
+        } else if (LIST) {
+            // one listed tetrahedron per lane: its id decodes like the ids below
+            const int64_t k = (int64_t)item * 32 + lane;
+            if (k < listed) {
+                const int64_t id = P.guard_list[k];
+                if (P.src == SRC_TETS) {
+                    unit = id;
+                } else {
+                    const int64_t u = id / 6;
+                    s_listed = (int)(id % 6);
+                    if (P.src == SRC_LATTICE) {
+                        ci = u % P.nc[0];
+                        cj = (u / P.nc[0]) % P.nc[1];
+                        ck = u / (P.nc[0] * P.nc[1]);
+                        unit = 1;
+                    } else if (cube_of_unit(P, u, ci, cj, ck)) {
+                        unit = u;
+                    }
+                }
+            }
         } else if (P.src == SRC_LATTICE) {
             // rows of 32 cubes along x
             const int64_t segs = (P.nc[0] + 31) / 32;
@@ -129,20 +154,23 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
             }
         }
 
-        const int nsub_item = is_chunk ? 1 : nsub;
-        for (int s = 0; s < nsub_item; ++s) {
+        const int nsub_item = (is_chunk || LIST) ? 1 : nsub;
+        for (int si = 0; si < nsub_item; ++si) {
+            const int s = LIST ? s_listed : si;
             // ---- 1. one tetrahedron per lane (or the queued tetrahedron's chunk on lane 0)
             int npairs = 0;
             double m_t = 0.0;
+            int64_t tid = 0;
+            bool to_list = false;
             if (is_chunk) {
                 npairs = chunk_setup<STATS, PASS>(P, S, lane, (int64_t)item, q, cnt);
                 __syncwarp();
             } else if (unit >= 0) {
                 P3<float> v[4];
                 int base[3];
-                // tetrahedron id as the bin pass numbers it
-                const int64_t tid = (P.src == SRC_TETS) ? unit
-                                    : 6 * ((P.src == SRC_LATTICE) ? ci + P.nc[0] * (cj + P.nc[1] * ck) : unit) + s;
+                // tetrahedron id as the bin pass numbers it (and the guarded-tetrahedron list)
+                tid = (P.src == SRC_TETS) ? unit
+                                          : 6 * ((P.src == SRC_LATTICE) ? ci + P.nc[0] * (cj + P.nc[1] * ck) : unit) + s;
                 if (P.src == SRC_TETS) {
                     explicit_tet<float>(P, unit, v, base);
                     m_t = P.tet_mass[unit];
@@ -198,6 +226,8 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
 #pragma unroll
                         for (int q = 0; q < 4; ++q) res[q] = mk<float>(0.f, 0.f, 0.f);
                         store_record(S, lane, ts, res, base, m_t, P.kappa_max, 0);
+                    } else {
+                        to_list = !BINNED;
                     }
                 } else {
                     // guarded: column runs, clipped in float64 from the exact vertices
@@ -211,6 +241,7 @@ __global__ void __launch_bounds__(kCoopThreads, MINB) k_warp_coop(const DepositP
                     store_record(S, lane, ts, res, base, m_t, P.kappa_max, 0);
                 }
             }
+            if (FIRST && !BINNED) list_guarded(P, to_list, tid, lane);
             // ---- 2. pair enumeration and clips
             coop_pairs<STATS, false, A, PASS>(P, S, lane, npairs, cnt);
             __syncwarp();
@@ -230,7 +261,8 @@ cudaError_t launch_coop_pass(const DepositParams &p, bool stats, int blocks_per_
     const int threads = kCoopThreads;
     constexpr bool GUARD = PASS == kPassGuard;
     const size_t smem = warp_smem_bytes(threads / 32, GUARD);
-    // the guarded pass (190 registers, float64 slots) runs 2 blocks per SM
+    // the guarded pass runs 2 blocks per SM (190 registers): its FP64 pipe is already the
+    // bottleneck there (84% busy), so more residency would not help
     const int minb = (stats || GUARD) ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
     const void *k;
     if constexpr (GUARD) {

@@ -423,9 +423,9 @@ PSE_HD double det6(const P3<double> (&p)[4])
 }
 
 // Overlap volume of a tetrahedron (cell frame, float64 vertices, either orientation)
-// with the cell, computed in float64: the redo path of the FP32 guard.  The vertices
-// must be the exact ones (not the float32-rounded set the FP32 clip used), otherwise
-// the redo only reproduces the rounding of the inputs.
+// with the cell, computed in float64: the guarded clip of the cell-by-cell schedules.  The
+// vertices must be the exact ones (not the float32-rounded set the FP32 clip used),
+// otherwise the float64 clip only reproduces the rounding of the inputs.
 PSE_HD double overlap_volume_fp64(P3<double> (&pd)[4])
 {
     if (det6(pd) < 0.0) {

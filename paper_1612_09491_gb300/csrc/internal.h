@@ -40,6 +40,9 @@ struct Workspace {
     unsigned long long queue_count;    // split tetrahedra appended by the bin pass (may exceed q_cap)
     unsigned long long n_chunk_items;  // work items of the split tetrahedra (0 if the queue overflowed)
     int queue_overflow;                // 1: the queue was too small; every tetrahedron goes the row path
+    // guarded tetrahedra the FP32 pass listed for the guarded pass (may exceed guard_cap:
+    // then the list is incomplete and the guarded pass scans every tetrahedron again)
+    unsigned long long guard_count;
 };
 
 constexpr size_t kWorkspaceBytes = 512;
@@ -89,6 +92,11 @@ struct DepositParams {
     int32_t chunk_cells;
     const struct CostModelDev *model;  // nullable: queue by the cost model's prediction
     uint32_t *qbits;           // cost model: bit t set = tetrahedron t was queued ([ceil(T/32)])
+    // warp and octree schedules: ids (unit * 6 + s, or the tetrahedron index) of the guarded
+    // multi-cell tetrahedra, appended by the FP32 pass; the guarded pass visits only these
+    // when all of them fit (guard_cap 0: no list, every tetrahedron is scanned again)
+    int64_t *guard_list;
+    int64_t guard_cap;
 };
 
 // warp kernels (every schedule but thread-per-tetrahedron): the float32 rounding residuals
@@ -99,7 +107,11 @@ struct DepositParams {
 constexpr int kMaxWarpBlocks = 1024;
 constexpr size_t kResidualBytes = (size_t)kMaxWarpBlocks * 4 * 12 * 32 * sizeof(float);
 
-// binned schedule: queue capacity and the bytes it takes after the residual blocks
+// the guarded-tetrahedron list of the warp and octree schedules, after the residual blocks
+constexpr int64_t kGuardListCap = int64_t(1) << 22;
+constexpr size_t kGuardListBytes = (size_t)kGuardListCap * 8;
+
+// binned schedule: queue capacity and the bytes it takes after the guarded-tetrahedron list
 constexpr int64_t kQueueCap = int64_t(1) << 21;
 constexpr size_t kQueueBytes = ((size_t)kQueueCap * (8 + 4) + (size_t)(kQueueCap + 1) * 8 + 255) / 256 * 256;
 // cost-model binning: one bit per tetrahedron after the queue

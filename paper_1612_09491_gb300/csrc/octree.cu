@@ -330,29 +330,44 @@ __global__ void __launch_bounds__(128) k_oct_thread(const DepositParams P)
 // ---------------------------------------------------------------------------
 // PASS kPassFp32 visits every (tetrahedron, leaf) pair: it counts the tetrahedra, deposits
 // degenerate ones and those inside one cell of a leaf, and clips the pairs below the guard by
-// column runs.  PASS kPassGuard visits the pairs again and clips only the guarded ones, cell
-// by cell in FP64.
+// column runs.  PASS kPassGuard visits the pairs again and clips only the guarded ones, by
+// column runs in FP64.
 template <bool STATS, int MINB, Acc A, int PASS>
 __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
 {
     constexpr bool FIRST = PASS == kPassFp32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem *S = reinterpret_cast<WarpSmem *>(smem_raw) + (threadIdx.x >> 5);
+    WarpSmem *S = warp_smem(!FIRST);
     bind_residuals(P, S, !FIRST);
     const int lane = threadIdx.x & 31;
     Counters cnt;
     if (STATS) cnt.zero();
     cnt.zero_mass();
     const int64_t bc = P.bc;
+    // the guarded pass: the tetrahedra the FP32 pass listed, 32 per item, when it listed all
+    const int64_t listed = FIRST ? -1 : listed_guarded(P);
+    const bool LIST = listed >= 0;
+    const int64_t n_items = LIST ? (listed + 31) / 32 : P.n_items;
 
     for (;;) {
         unsigned long long item = 0;
         if (lane == 0) item = atomicAdd(FIRST ? &P.ws->work_counter : &P.ws->work_counter2, 1ull);
         item = __shfl_sync(kFull, item, 0);
-        if ((int64_t)item >= P.n_items) break;
+        if ((int64_t)item >= n_items) break;
         int64_t ci = 0, cj = 0, ck = 0;
+        int s_listed = 0;
         bool have = false;
-        if (P.src == SRC_LATTICE) {
+        if (LIST) {
+            const int64_t k = (int64_t)item * 32 + lane;
+            if (k < listed) {  // id = 6 (ci + nc0 (cj + nc1 ck)) + s, whatever the source
+                const int64_t id = P.guard_list[k];
+                const int64_t c = id / 6;
+                s_listed = (int)(id % 6);
+                ci = c % P.nc[0];
+                cj = (c / P.nc[0]) % P.nc[1];
+                ck = c / (P.nc[0] * P.nc[1]);
+                have = true;
+            }
+        } else if (P.src == SRC_LATTICE) {
             const int64_t segs = (P.nc[0] + 31) / 32;
             const int64_t row = (int64_t)item / segs, seg = (int64_t)item % segs;
             const int64_t i = seg * 32 + lane;
@@ -369,7 +384,9 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                 if (!have) set_error(P.ws, 3, (int)(u & 0x7fffffff));
             }
         }
-        for (int s = 0; s < 6; ++s) {
+        for (int si = 0; si < (LIST ? 1 : 6); ++si) {
+            const int s = LIST ? s_listed : si;
+            bool to_list = false;  // the FP32 pass: a pair of this tetrahedron is guarded
             float x[4][3];
             int k[4][3];
             double cen[3] = {0.0, 0.0, 0.0};
@@ -446,6 +463,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                                 set_error(P.ws, 2, lane);
                             } else if (FIRST && guard) {
                                 // left to the guarded pass; counted here
+                                to_list = true;
                                 if (STATS) { cnt.u[ST_BBOX_CELLS] += ncell; cnt.u[ST_BIN0 + size_bin(ncell)]++; }
                             } else if (ncell > 0) {
                                 npairs = (int)run_count(dim, ts.axis);
@@ -494,6 +512,7 @@ __global__ void __launch_bounds__(128, MINB) k_oct_warp(const DepositParams P)
                 __syncwarp();
             }
             __syncwarp();
+            if (FIRST) list_guarded(P, to_list, 6 * (ci + P.nc[0] * (cj + P.nc[1] * ck)) + s, lane);
         }
     }
     if (STATS) cnt.flush(P.ws);
@@ -797,7 +816,8 @@ cudaError_t launch_oct_pass(const DepositParams &p, bool stats, int blocks_per_s
     const int threads = 128;
     constexpr bool GUARD = PASS == kPassGuard;
     const size_t smem = warp_smem_bytes(threads / 32, GUARD);
-    // the guarded pass (190 registers, float64 slots) runs 2 blocks per SM
+    // the guarded pass runs 2 blocks per SM (190 registers): its FP64 pipe is already the
+    // bottleneck there (84% busy), so more residency would not help
     const int minb = (stats || GUARD) ? 2 : (blocks_per_sm >= 4 ? 4 : (blocks_per_sm == 3 ? 3 : 2));
     const void *k;
     if constexpr (GUARD) {

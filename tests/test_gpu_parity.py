@@ -597,3 +597,41 @@ def test_stats_overlapped_cells_and_mass_out():
             assert 0 < st["column_runs"] and st["partial_clips"] - st["fp64_redos"] <= 2 * st["column_runs"]
         else:
             assert st["column_runs"] == 0
+
+
+@pytest.mark.parametrize("grid", ["uniform", "octree", "uniform-streamed"])
+def test_guarded_list_and_full_rescan_agree(grid):
+    """The guarded pass visits only the tetrahedra the FP32 pass listed, or (list disabled, or
+    more guarded tetrahedra than the list holds) scans every tetrahedron again.  The three give
+    the same deposit and the same counters, on a shell-crossed lattice where about a quarter of
+    the tetrahedra are guarded."""
+    n, g = 24, 48
+    pos = zeldovich_positions(n, -1.5, 3.0, seed=31)
+    dpos = dev(pos)
+    if grid == "octree":
+        oct_ = pse.build_octree_from_tet_sizes(dpos, n, 8, 3, 2.0)
+
+    def run(cap):
+        tu = {"blocks_per_sm": 4, "guard_list_cap": cap}
+        if grid == "octree":
+            m, st = pse.deposit_octree(dpos, n, oct_, stats=True, tuning=tu, mass_fixup=False)
+        elif grid == "uniform":
+            m, st = pse.deposit_uniform(dpos, n, g, stats=True, tuning=tu, mass_fixup=False)
+        else:
+            m, st = pse.deposit_uniform_streamed(torch.from_numpy(pos).pin_memory(), n, g, 5, stats=True,
+                                                 tuning=tu, mass_fixup=False)
+        return m.cpu().numpy(), st
+
+    ref, st_ref = run(0)        # the list (default capacity)
+    assert st_ref["fp64_redos"] > 0.1 * st_ref["partial_clips"]
+    for cap in (-1, 1000):      # no list; a list too small for this lattice
+        m, st = run(cap)
+        e = cell_errors(m, ref)
+        assert e["max_rel"] <= 1e-12 and e["mass"] <= 1e-13, (cap, e)
+        for k in ("tets", "partial_clips", "fp64_redos", "column_runs", "overlapped_cells", "bbox_cells"):
+            assert st[k] == st_ref[k], (cap, k, st[k], st_ref[k])
+    if grid != "uniform-streamed":
+        o, _ = (oracle.deposit_octree(pos, n, oct_.leaves(), 8, 3) if grid == "octree"
+                else oracle.deposit_lattice(pos, n, g))
+        e = cell_errors(ref, o)
+        assert e["max_rel"] <= TOL32, e

@@ -104,3 +104,38 @@ def test_noalloc_build_truncates_at_cap_and_builds_one_level(L):
     np.testing.assert_array_equal(buf, exp[:cap])  # and the first cap leaves
     root = noalloc_leaves(L, pos, n, bc, 0)        # max_level 0: the root alone
     np.testing.assert_array_equal(root, [[0, 0, 0, 0]])
+
+
+def test_noalloc_build_captured_in_a_graph_and_replayed(L):
+    """The stated use: after one call outside capture (which resolves the scratch array's
+    address), the call is captured in a CUDA graph and replayed; each replay writes the
+    leaves of the allocating build for the positions the graph reads at that moment."""
+    n, bc, ml = 16, 4, 4
+    pos_a = squeezed_lattice(n, (0.3, 0.6, 0.4), seed=1)
+    pos_b = squeezed_lattice(n, (0.7, 0.2, 0.5), seed=2)
+    exp_a = pse.build_octree_from_tet_sizes(torch.from_numpy(pos_a).cuda(), n, bc, ml, 2.0).leaves()
+    exp_b = pse.build_octree_from_tet_sizes(torch.from_numpy(pos_b).cuda(), n, bc, ml, 2.0).leaves()
+    noalloc_leaves(L, pos_a, n, bc, ml)  # first call, outside capture
+    dpos = torch.from_numpy(pos_a).cuda()
+    lat = pse.lattice(n)
+    cap = 8 ** 4
+    d_leaves = torch.full((cap, 4), -1, dtype=torch.int32, device="cuda")
+    d_n = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            rc = L.pse_build_octree_leaves_noalloc(ctypes.c_void_p(dpos.data_ptr()), ctypes.byref(lat), bc, ml, 2.0,
+                                                   ctypes.c_void_p(d_leaves.data_ptr()), cap,
+                                                   ctypes.c_void_p(d_n.data_ptr()), ctypes.c_void_p(side.cuda_stream))
+    assert rc == _lib.PSE_OK, L.pse_last_error().decode()
+    torch.cuda.current_stream().wait_stream(side)
+    for pos, exp in ((pos_a, exp_a), (pos_b, exp_b)):
+        dpos.copy_(torch.from_numpy(pos))
+        d_leaves.fill_(-1)
+        graph.replay()
+        torch.cuda.synchronize()
+        count = int(d_n.item())
+        assert count == len(exp)
+        np.testing.assert_array_equal(d_leaves[:count].cpu().numpy(), exp)
