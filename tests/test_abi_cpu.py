@@ -83,8 +83,8 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu\n", sizeof(pse_deposit_stats), offsetof(pse_deposit_stats, bin_counts),
          offsetof(pse_deposit_stats, mass_dropped), offsetof(pse_deposit_stats, overlapped_cells),
          offsetof(pse_deposit_stats, mass_out));
-  printf("%zu %zu %zu %zu\n", sizeof(pse_tuning), offsetof(pse_tuning, split_cells),
-         offsetof(pse_tuning, chunk_cells), offsetof(pse_tuning, use_graph));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(pse_tuning), offsetof(pse_tuning, split_cells),
+         offsetof(pse_tuning, chunk_cells), offsetof(pse_tuning, use_graph), offsetof(pse_tuning, guard_list_cap));
   return 0;
 }
 ''')
@@ -98,7 +98,9 @@ int main(void) {
     assert got[2] == [ctypes.sizeof(S), S.bin_counts.offset, S.mass_dropped.offset, S.overlapped_cells.offset,
                       S.mass_out.offset]
     Tu = _lib.Tuning
-    assert got[3] == [ctypes.sizeof(Tu), Tu.split_cells.offset, Tu.chunk_cells.offset, Tu.use_graph.offset]
+    assert got[3] == [ctypes.sizeof(Tu), Tu.split_cells.offset, Tu.chunk_cells.offset, Tu.use_graph.offset,
+                      Tu.guard_list_cap.offset]
+    assert got[3][0] == 40  # the field took a reserved slot: the struct keeps its size
 
 
 def test_abi_version(L):
