@@ -526,84 +526,121 @@ __device__ __forceinline__ int64_t hist_offset(int level) { return (int64_t)64 *
 
 // One pass over the tetrahedra: per level 0 .. max_level-1, the node that holds the
 // tetrahedron's vertex centroid and the 64-bin log10 histogram bin of its mean edge length
-// in that level's cells.  The edge vectors are the unwrapped vertex offsets from vertex 0,
-// formed in float64 and rounded to float32 (a bin is 24% wide); the 32 tetrahedra of a warp
-// are neighbours, so equal (node, bin) keys are merged in the warp before one atomic per key.
+// in that level's cells.  A lane takes one Lagrangian cube (a warp: 32 neighbouring cubes of a
+// row) and its 6 Kuhn tetrahedra, which all start at corner 000: the 7 other corners are
+// loaded once, unwrapped once (offsets from corner 000 formed in float64 and rounded to
+// float32; a bin is 24% wide), and the 19 distinct edges serve all 6 tetrahedra.  The
+// centroid is summed in float64 from the same offsets, and the nodes of the coarser levels
+// are the finest level's node coordinates shifted (scaling by 2^l commutes with rounding).
+// Equal (node, bin) keys are merged in the warp before one atomic per key.
 __global__ void __launch_bounds__(256) k_tet_size_hist(const DepositParams P, unsigned *__restrict__ hist)
 {
     __shared__ unsigned sh[64 + 512];  // levels 0 and 1 aggregated per block
     for (int i = threadIdx.x; i < 576; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int64_t n_tets = 6 * P.n_units;
     const int levels = P.max_level;  // decisions are made for levels 0 .. max_level-1
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const double inv_box = 1.0 / P.box;
+    const float h0 = (float)(P.box / (double)P.bc);
+    const bool rows = P.src == SRC_LATTICE;
+    const int64_t segs = (P.nc[0] + 31) / 32;
+    const int64_t n_items = rows ? segs * P.nc[1] * P.nc[2] : (P.n_units + 31) / 32;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int top = levels > 0 ? levels - 1 : 0;  // the finest decision level
+    const double top_scale = (double)((int64_t)1 << top);
     // whole warps iterate together (the merge below needs every lane)
-    for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < n_tets; t0 += stride) {
-        const int64_t t = t0 + lane;
+    for (int64_t item = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); item < n_items; item += warps) {
+        int64_t ci = 0, cj = 0, ck = 0;
         bool ok = false;
-        float me = 0.f;        // mean edge length in level-0 cells
-        double cen[3] = {0.0, 0.0, 0.0};
-        if (t < n_tets) {
-            int64_t ci, cj, ck;
-            if (cube_of_unit(P, t / 6, ci, cj, ck)) {
+        if (rows) {
+            const int64_t row = item / segs, i = (item % segs) * 32 + lane;
+            if (i < P.nc[0]) {
+                ci = i;
+                cj = row % P.nc[1];
+                ck = row / P.nc[1];
                 ok = true;
-                float x[4][3];
-                int k[4][3];
-                lattice_tet_raw(P, ci, cj, ck, (int)(t % 6), x, k);
-                float r[4][3];
+            }
+        } else {
+            const int64_t u = item * 32 + lane;
+            ok = u < P.n_units && cube_of_unit(P, u, ci, cj, ck);
+        }
+        // corner c = (bit 0: +x, bit 1: +y, bit 2: +z): offsets from corner 000
+        float x0[3] = {0.f, 0.f, 0.f}, r[8][3];
+        double d[8][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { r[0][a] = 0.f; d[0][a] = 0.0; }
+        if (ok) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                int64_t i = ci + (c & 1), j = cj + ((c >> 1) & 1), kk = ck + ((c >> 2) & 1);
+                if (P.periodic) {
+                    i = wrap_idx(i, P.n[0]);
+                    j = wrap_idx(j, P.n[1]);
+                    if (!P.slab) kk = wrap_idx(kk, P.n[2]);
+                }
+                const float *pp = P.pos + 3 * (i + P.n[0] * (j + P.n[1] * kk));
+                float x[3] = {__ldg(pp), __ldg(pp + 1), __ldg(pp + 2)};
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    r[0][a] = 0.f;
-                    double sum = 0.0;
-#pragma unroll
-                    for (int q = 1; q < 4; ++q) {
-                        const double d = ((double)x[q][a] - (double)x[0][a]) + (double)k[q][a] * P.box;
-                        r[q][a] = (float)d;
-                        sum += d;
+                    if (c == 0) {
+                        x0[a] = x[a];
+                    } else {
+                        const double raw = (double)x[a] - (double)x0[a];
+                        const int sh = P.periodic ? ((raw >= 0.5 * P.box) ? -1 : ((raw < -0.5 * P.box) ? 1 : 0)) : 0;
+                        d[c][a] = raw + (double)sh * P.box;
+                        r[c][a] = (float)d[c][a];
                     }
-                    cen[a] = (double)x[0][a] + 0.25 * sum;
-                    cen[a] -= P.box * floor(cen[a] * inv_box);
-                    if (!(cen[a] < P.box) || !(cen[a] >= 0.0)) cen[a] = 0.0;
                 }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            int o1[3], o2[3];
+            kuhn_offsets(s, o1, o2);
+            const int c1 = o1[0] | (o1[1] << 1) | (o1[2] << 2), c2 = o2[0] | (o2[1] << 1) | (o2[2] << 2);
+            const int cq[4] = {0, c1, c2, 7};
+            float me = 0.f;  // mean edge length in level-0 cells
+            int64_t top_c[3] = {0, 0, 0};
+            if (ok) {
                 float es = 0.f;
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
 #pragma unroll
                     for (int b = a + 1; b < 4; ++b) {
-                        const float dx = r[b][0] - r[a][0], dy = r[b][1] - r[a][1], dz = r[b][2] - r[a][2];
+                        const float dx = r[cq[b]][0] - r[cq[a]][0], dy = r[cq[b]][1] - r[cq[a]][1],
+                                    dz = r[cq[b]][2] - r[cq[a]][2];
                         es += sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
                     }
-                const float h0 = (float)(P.box / (double)P.bc);
                 me = es * (1.f / 6.f) / h0;
-            }
-        }
-        for (int l = 0; l < levels; ++l) {
-            unsigned long long key = ~0ull - (unsigned long long)lane;  // lanes without a tetrahedron match nothing
-            int bin = 0;
-            int64_t node = 0;
-            if (ok) {
-                const int64_t nn = (int64_t)1 << l;
-                int64_t stride_n = 1;
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
-                    int64_t c = (int64_t)floor(cen[a] * (double)nn * inv_box);
-                    c = c < 0 ? 0 : (c >= nn ? nn - 1 : c);
-                    node += c * stride_n;
-                    stride_n *= nn;
+                    double cen = (double)x0[a] + 0.25 * ((d[c1][a] + d[c2][a]) + d[7][a]);
+                    cen -= P.box * floor(cen * inv_box);
+                    if (!(cen < P.box) || !(cen >= 0.0)) cen = 0.0;
+                    int64_t c = (int64_t)floor(cen * top_scale * inv_box);
+                    const int64_t nn = (int64_t)1 << top;
+                    top_c[a] = c < 0 ? 0 : (c >= nn ? nn - 1 : c);
                 }
-                // a level-l cell is 2^-l of a level-0 cell (an exact float scaling)
-                bin = (int)floorf((log10f(ldexpf(me, l)) + 3.0f) * (64.0f / 6.0f));
-                bin = bin < 0 ? 0 : (bin > 63 ? 63 : bin);
-                key = (unsigned long long)node * 64 + (unsigned long long)bin;
             }
-            const unsigned peers = __match_any_sync(kFull, key);
-            if (ok && lane == __ffs(peers) - 1) {
-                const unsigned c = (unsigned)__popc(peers);
-                if (l == 0) atomicAdd(&sh[bin], c);
-                else if (l == 1) atomicAdd(&sh[64 + node * 64 + bin], c);
-                else atomicAdd(&hist[hist_offset(l) + node * 64 + bin], c);
+            for (int l = 0; l < levels; ++l) {
+                unsigned long long key = ~0ull - (unsigned long long)lane;  // lanes without a cube match nothing
+                int bin = 0;
+                int64_t node = 0;
+                if (ok) {
+                    const int sh = top - l;
+                    node = (top_c[0] >> sh) + ((top_c[1] >> sh) << l) + ((top_c[2] >> sh) << (2 * l));
+                    // a level-l cell is 2^-l of a level-0 cell (an exact float scaling)
+                    bin = (int)floorf((log10f(ldexpf(me, l)) + 3.0f) * (64.0f / 6.0f));
+                    bin = bin < 0 ? 0 : (bin > 63 ? 63 : bin);
+                    key = (unsigned long long)node * 64 + (unsigned long long)bin;
+                }
+                const unsigned peers = __match_any_sync(kFull, key);
+                if (ok && lane == __ffs(peers) - 1) {
+                    const unsigned cnt = (unsigned)__popc(peers);
+                    if (l == 0) atomicAdd(&sh[bin], cnt);
+                    else if (l == 1) atomicAdd(&sh[64 + node * 64 + bin], cnt);
+                    else atomicAdd(&hist[hist_offset(l) + node * 64 + bin], cnt);
+                }
             }
         }
     }
@@ -798,7 +835,7 @@ cudaError_t launch_node_counts(const double *boxes, int64_t nb, const int32_t *n
 cudaError_t launch_octree_hist(const DepositParams &p, unsigned *hist, cudaStream_t st)
 {
     const int threads = 256;
-    const int64_t n = 6 * p.n_units;
+    const int64_t n = p.n_units;  // one lane per cube
     int64_t blocks = (n + threads - 1) / threads;
     const int64_t cap = (int64_t)persistent_blocks((const void *)k_tet_size_hist, threads, 0) * 4;
     if (blocks > cap) blocks = cap;
