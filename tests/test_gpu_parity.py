@@ -599,24 +599,31 @@ def test_stats_overlapped_cells_and_mass_out():
             assert st["column_runs"] == 0
 
 
-@pytest.mark.parametrize("grid", ["uniform", "octree", "uniform-streamed"])
+@pytest.mark.parametrize("grid", ["uniform", "octree", "uniform-streamed", "uniform-subset", "octree-subset"])
 def test_guarded_list_and_full_rescan_agree(grid):
     """The guarded pass visits only the tetrahedra the FP32 pass listed, or (list disabled, or
     more guarded tetrahedra than the list holds) scans every tetrahedron again.  The three give
     the same deposit and the same counters, on a shell-crossed lattice where about a quarter of
-    the tetrahedra are guarded."""
+    the tetrahedra are guarded; the subset cases take a shuffled list of cube ids, whose
+    listed ids decode differently from a whole lattice's."""
     n, g = 24, 48
     pos = zeldovich_positions(n, -1.5, 3.0, seed=31)
     dpos = dev(pos)
-    if grid == "octree":
+    ids = np.random.default_rng(3).permutation(n ** 3)[: n ** 3 // 3]
+    dids = torch.from_numpy(ids.astype(np.int64)).cuda()
+    if grid.startswith("octree"):
         oct_ = pse.build_octree_from_tet_sizes(dpos, n, 8, 3, 2.0)
 
     def run(cap):
         tu = {"blocks_per_sm": 4, "guard_list_cap": cap}
         if grid == "octree":
             m, st = pse.deposit_octree(dpos, n, oct_, stats=True, tuning=tu, mass_fixup=False)
+        elif grid == "octree-subset":
+            m, st = pse.deposit_octree(dpos, n, oct_, stats=True, tuning=tu, mass_fixup=False, cube_ids=dids)
         elif grid == "uniform":
             m, st = pse.deposit_uniform(dpos, n, g, stats=True, tuning=tu, mass_fixup=False)
+        elif grid == "uniform-subset":
+            m, st = pse.deposit_uniform(dpos, n, g, stats=True, tuning=tu, mass_fixup=False, cube_ids=dids)
         else:
             m, st = pse.deposit_uniform_streamed(torch.from_numpy(pos).pin_memory(), n, g, 5, stats=True,
                                                  tuning=tu, mass_fixup=False)
@@ -630,8 +637,17 @@ def test_guarded_list_and_full_rescan_agree(grid):
         assert e["max_rel"] <= 1e-12 and e["mass"] <= 1e-13, (cap, e)
         for k in ("tets", "partial_clips", "fp64_redos", "column_runs", "overlapped_cells", "bbox_cells"):
             assert st[k] == st_ref[k], (cap, k, st[k], st_ref[k])
-    if grid != "uniform-streamed":
+    if grid in ("uniform", "octree"):
         o, _ = (oracle.deposit_octree(pos, n, oct_.leaves(), 8, 3) if grid == "octree"
                 else oracle.deposit_lattice(pos, n, g))
         e = cell_errors(ref, o)
         assert e["max_rel"] <= TOL32, e
+    elif grid.endswith("subset"):  # the subset's own deposit, against the oracle on the same cubes
+        o, _ = (oracle.deposit_octree(pos, n, oct_.leaves(), 8, 3, cube_ids=np.sort(ids)) if grid == "octree-subset"
+                else oracle.deposit_lattice(pos, n, g, cube_ids=np.sort(ids)))
+        e = cell_errors(ref, o)
+        assert e["mass"] <= 1e-6, e  # no renormalisation here: the FP32 clips' own sum
+        if grid == "uniform-subset":
+            tets = subset_tets(pos, n, np.sort(ids))
+            e = cell_errors(ref, o, floor_mass=density_floor(tets, np.full(len(tets), 1.0 / (6 * n ** 3)), g))
+            assert e["max_rel"] <= TOL32, e
