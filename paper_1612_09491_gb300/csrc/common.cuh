@@ -487,15 +487,24 @@ __device__ __forceinline__ int64_t run_count(const int (&dim)[3], int C)
 }
 
 // Run (ia, ib, w) of record t: base-frame first cell (cx, cy, cz) and length kw.
+// (la, lb, lc: the same first cell along the axes A, B and C.)
 __device__ __forceinline__ void run_cells(const WarpSmem *S, int t, int ia, int ib, int w, int &cx, int &cy, int &cz,
-                                          int &kw)
+                                          int &kw, int &la, int &lb, int &lc)
 {
     const int C = S->axis[t], A = axis_a(C), B = axis_b(C);
     kw = min(kRun, S->dim[C][t] - w * kRun);
-    const int la = S->lo[A][t] + ia, lb = S->lo[B][t] + ib, lc = S->lo[C][t] + w * kRun;
+    la = S->lo[A][t] + ia;
+    lb = S->lo[B][t] + ib;
+    lc = S->lo[C][t] + w * kRun;
     cx = C == 0 ? lc : (C == 1 ? lb : la);
     cy = C == 1 ? lc : (C == 2 ? lb : la);
     cz = C == 2 ? lc : (C == 0 ? lb : la);
+}
+__device__ __forceinline__ void run_cells(const WarpSmem *S, int t, int ia, int ib, int w, int &cx, int &cy, int &cz,
+                                          int &kw)
+{
+    int la, lb, lc;
+    run_cells(S, t, ia, ib, w, cx, cy, cz, kw, la, lb, lc);
 }
 
 // Run number `local` of record t (ia fastest, then ib, then w).
@@ -517,21 +526,24 @@ __device__ __forceinline__ bool dims_fit_queue(const int (&dim)[3])
     return dim[0] < (1 << 19) && dim[1] < (1 << 19) && dim[2] < (1 << 19);
 }
 
-// Record t as column_volumes reads it: vertices relative to the run's first cell (fx, fy,
-// fz) and normals, relabelled so that the divergence axis C is z, read from shared memory.
+// Unguarded record t as the column clip reads it: vertices relative to the run's first cell
+// and relabelled so that axis C is z (to_axis), face normals likewise.  The relabelling is
+// bound once per run as three row pointers, (C+1)%3, (C+2)%3 and C, into the record arrays
+// (vertex or face i is 3 rows = 96 floats further on; the normals follow the vertices at
+// 12 rows = 384 floats), so a fetch is three loads at fixed offsets and no selects.
 struct RecordRun {
-    const WarpSmem *S;
-    int t, C;
-    float fx, fy, fz;
+    const float *va, *vb, *vc;  // &S->v[row][t] for the three rows
+    float fa, fb, fc;           // the run's first cell along the same three axes
     __device__ __forceinline__ P3<float> vtx(int i) const
     {
-        return to_axis(mk<float>(S->v[3 * i][t] - fx, S->v[3 * i + 1][t] - fy, S->v[3 * i + 2][t] - fz), C);
+        return mk<float>(va[96 * i] - fa, vb[96 * i] - fb, vc[96 * i] - fc);
     }
     __device__ __forceinline__ P3<float> nrm(int f) const
     {
-        return to_axis(mk<float>(S->n[3 * f][t], S->n[3 * f + 1][t], S->n[3 * f + 2][t]), C);
+        return mk<float>(va[384 + 96 * f], vb[384 + 96 * f], vc[384 + 96 * f]);
     }
 };
+static_assert(offsetof(WarpSmem, n) == offsetof(WarpSmem, v) + 384 * sizeof(float), "RecordRun reads n after v");
 
 // Guarded record t as the guarded pass's column clip reads it: the exact vertices (float32
 // vertex plus its rounding residual) in float64, in the exact tetrahedron's positive
@@ -657,13 +669,15 @@ __device__ __forceinline__ void run_round(const DepositParams &P, WarpSmem *S, i
         const int t = (int)(ent & 31u);
         const int w = (int)((ent >> (5 + 2 * kQBits)) & kQMask);
         const int C = S->axis[t];
-        int cx, cy, cz, kw;
-        run_cells(S, t, (int)((ent >> 5) & kQMask), (int)((ent >> (5 + kQBits)) & kQMask), w, cx, cy, cz, kw);
+        int cx, cy, cz, kw, la, lb, lc;
+        run_cells(S, t, (int)((ent >> 5) & kQMask), (int)((ent >> (5 + kQBits)) & kQMask), w, cx, cy, cz, kw, la, lb,
+                  lc);
         if (STATS) cnt.u[ST_RUNS]++;
         const bool lo_open = w > 0 || S->cut[t] != 0;
         double vol[kRun];
         if constexpr (sizeof(T) == sizeof(float)) {
-            const RecordRun src{S, t, C, (float)cx, (float)cy, (float)cz};
+            // rows (C+1)%3 = A, (C+2)%3 = B and C, and the run's first cell along them
+            const RecordRun src{&S->v[axis_a(C)][t], &S->v[axis_b(C)][t], &S->v[C][t], (float)la, (float)lb, (float)lc};
             float v32[kRun];
             column_volumes<kRun>(src, S->lx[t], S->ly[t], kw, lo_open, v32, &S->poly[0][lane]);
 #pragma unroll
