@@ -21,7 +21,7 @@ blocks (the call overwrites them, FP32 clips renormalised to the exact total mas
   the lattice, and the 128^3 precision workload (FP32 vs FP64 vs the oracle's full deposit)
   and the 512^3 cost-model workload.
 
-``--config 2|3|4`` prints the line of another workload alone; ``--impl reference`` times the
+``--config 2|3|4|6|7`` prints the line of another workload alone; ``--impl reference`` times the
 oracle alone (host cores).  Prints one JSON line on rank 0.
 """
 from __future__ import annotations
@@ -905,7 +905,10 @@ def run_octree256(args, cfg):
               "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
               "config": {"workload": cfg.name, "particles": f"{n}^3", "tets": cfg.n_tets,
-                         "grid": f"octree bc={cfg.bc} levels 0-{cfg.max_level}", "leaves": int(oct_.n_leaves),
+                         "grid": f"octree bc={cfg.bc} levels 0-{cfg.max_level} (finest {cfg.grid_n}^3)",
+                         "collapsed_regions": ({"regions": cfg.collapse[0], "R": cfg.collapse[1], "R2": cfg.collapse[2],
+                                                "f": cfg.collapse[3]} if cfg.collapse else None),
+                         "leaves": int(oct_.n_leaves),
                          "leaf_levels": {int(l): int(c) for l, c in
                                          zip(*np.unique(oct_.leaves()[:, 0], return_counts=True))},
                          "tuning": tuned, "autotune_ms": tune_ms, "precision": PRECISION,
@@ -930,7 +933,7 @@ def main():
         return
     if args.config == 5:
         run_scale(args, cfg)
-    elif args.config in (3, 6):
+    elif args.config in (3, 6, 7):
         run_octree256(args, cfg)
     else:
         import torch

@@ -7,6 +7,7 @@ volumes.  Both sides of every parity test read their inputs from here.
 from .lattice import (  # noqa: F401
     CONFIGS,
     WorkloadConfig,
+    collapse_positions,
     config_positions,
     jitter_positions,
     lattice_positions,

@@ -17,6 +17,14 @@ Three families of positions:
   paper deposits (Dark Sky early data release, Sec. 7), which are not available.
 * ``jitter_positions``: the paper's weak-scaling input (Sec. 7.2): lattice plus
   independent uniform offsets of up to one lattice spacing per axis.
+* ``collapse_positions``: a Zel'dovich field with collapsed regions added, so that the
+  tetrahedra span a wide range of sizes and a tree refined by tetrahedron size is genuinely
+  adaptive (the Zel'dovich field alone is quasi-linear: its tetrahedra are too alike in size
+  for the octree to stop above the finest level anywhere but everywhere).  Around each of a
+  few seeded centres, the offset d from the centre (minimum image) is scaled radially: by f
+  inside the Lagrangian radius R (a uniform core f^-3 times denser), then linearly in |d| from
+  f R at R to R2 at R2 (an underdense shell), unchanged beyond R2.  The map is continuous,
+  so no tetrahedron tears; regions are applied one after another.
 
 Recipe for the Zel'dovich field (the reading used throughout this project):
 white noise w ~ N(0,1) on the n^3 lattice (numpy PCG64, the given seed);
@@ -45,6 +53,7 @@ class WorkloadConfig:
     grid_n: int  # uniform: cells per side; octree: finest equivalent cells per side
     bc: int = 0  # octree: cells per leaf block side
     max_level: int = 0  # octree: deepest refinement level
+    collapse: tuple = ()  # (regions, R, R2, f) of collapse_positions, box units; () = none
 
     @property
     def seed(self) -> int:
@@ -66,6 +75,10 @@ CONFIGS = {
     # spacings) grows as 1/n, so rms 1.5 at 256^3 matches rms 3 at 1024^3.  The case that
     # profilers capture in full.
     6: WorkloadConfig(6, "profile-256c-octree32", 256, -2.0, 1.5, "octree", 512, bc=32, max_level=4),
+    # workload 6's field with 8 collapsed regions, on 4 finest cells per lattice spacing: field
+    # tetrahedra stop refining at level 3, the collapsed cores refine to level 4
+    7: WorkloadConfig(7, "halos-256c-octree64", 256, -2.0, 1.5, "octree", 1024, bc=64, max_level=4,
+                      collapse=(8, 0.1, 0.16, 0.35)),
 }
 
 
@@ -133,11 +146,33 @@ def zeldovich_positions(n: int, spectral_index: float, rms_disp: float, seed: in
     return _wrap_f32(_lagrangian_q(n, box, 0.0) + psi, box)
 
 
+def collapse_positions(pos: np.ndarray, regions: int, radius: float, radius2: float, factor: float, seed: int,
+                       box: float = 1.0) -> np.ndarray:
+    """`pos` (float32 [N, 3] in [0, box)) with `regions` collapsed regions at seeded centres (the
+    recipe in the module doc; radii in box units), float32 [N, 3] wrapped into [0, box)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = pos.astype(np.float64)
+    for c in rng.random((regions, 3)) * box:
+        d = x - c
+        d -= box * np.round(d / box)
+        r = np.linalg.norm(d, axis=1)
+        s = np.ones_like(r)
+        s[r < radius] = factor
+        ramp = (r >= radius) & (r < radius2)
+        s[ramp] = (factor * radius + (r[ramp] - radius) * (radius2 - factor * radius) / (radius2 - radius)) / r[ramp]
+        x += d * (s - 1.0)[:, None]
+    return _wrap_f32(x, box)
+
+
 def config_positions(cfg: WorkloadConfig | int, box: float = 1.0) -> np.ndarray:
     """Positions of one of the numbered workloads (seed = 1000 + index)."""
     if isinstance(cfg, int):
         cfg = CONFIGS[cfg]
-    return zeldovich_positions(cfg.n, cfg.spectral_index, cfg.rms_disp, cfg.seed, box)
+    pos = zeldovich_positions(cfg.n, cfg.spectral_index, cfg.rms_disp, cfg.seed, box)
+    if cfg.collapse:
+        regions, r1, r2, f = cfg.collapse
+        pos = collapse_positions(pos, regions, r1 * box, r2 * box, f, cfg.seed + 1, box)
+    return pos
 
 
 def random_dyadic_tets(count: int, seed: int, span: float = 3.0, denom_bits: int = 6,

@@ -239,3 +239,26 @@ def test_count_rule_build_matches_oracle():
         assert not near
         np.testing.assert_array_equal(got, exp)
         assert len(set(exp[:, 0].tolist())) > 1  # the squeezed region refines deeper
+
+
+def test_collapsed_regions_give_an_adaptive_tree_and_match_the_oracle():
+    """The collapsed-region input of workload 7 at a small size (4 finest cells per lattice
+    spacing): the field's tetrahedra stop refining a level above the finest, the collapsed
+    cores refine to the finest level, the GPU build agrees with the oracle away from the
+    threshold, and the deposit on that mixed-level tree matches the oracle's."""
+    from pse_inputs import collapse_positions
+    n, bc, ml = 32, 8, 4
+    pos = collapse_positions(zeldovich_positions(n, -2.0, 1.5 * (n / 256) ** 0.5, seed=1007), 8, 0.1, 0.16, 0.35,
+                             1008)
+    got, exp, near = _tree_agreement(pos, n, bc, ml)
+    levels = np.bincount(got[:, 0], minlength=ml + 1)
+    assert levels[ml] > 0 and levels[ml - 1] > 0, levels  # mixed levels
+    gs, es = {tuple(r) for r in got.tolist()}, {tuple(r) for r in exp.tolist()}
+
+    def under(leaf, node):
+        return leaf[0] >= node[0] and all((leaf[1 + a] >> (leaf[0] - node[0])) == node[1 + a] for a in range(3))
+    assert all(any(under(l, nd) for nd in near) for l in gs ^ es), (gs ^ es, near)
+    ref, _ = oracle.deposit_octree(pos, n, got, bc, ml)
+    m, st = gpu_octree_deposit(pos, n, got, bc, ml, pse.PSE_FP32_FP64ACC, pse.PSE_WARP_COOPERATIVE, stats=True)
+    e = cell_errors(m, ref)
+    assert e["max_rel"] <= 1e-5 and e["mass"] <= 1e-12, e
